@@ -1,0 +1,748 @@
+/*
+ * Plain FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Every routine loops over elements in natural order and over quadrature
+ * points in rule order, exactly in the gather / gradient / density /
+ * integrate / accumulate sequence of Algorithm 1 (arXiv 2602.12365, Sec. 2),
+ * with no blocking, fusion or reordering.  Nodal sums use plain +=; the total
+ * energy uses Neumaier compensated summation.  Single threaded.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXEN 8
+#define MAXD 3
+
+int ora_n_en(int etype) { return etype == 0 ? 3 : (etype == 1 ? 4 : 8); }
+int ora_dim(int etype) { return etype == 0 ? 2 : 3; }
+int ora_n_qp(int etype) { return etype == 2 ? 8 : 1; }
+
+/* ------------------------------------------------------------------------ */
+/* small dense helpers (row-major d x d)                                    */
+/* ------------------------------------------------------------------------ */
+static double det_d(int d, const double* A) {
+    if (d == 2) return A[0] * A[3] - A[1] * A[2];
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse by the adjugate divided by the determinant */
+static void inv_d(int d, const double* A, double* Ai) {
+    double J = det_d(d, A);
+    if (d == 2) {
+        Ai[0] = A[3] / J;
+        Ai[1] = -A[1] / J;
+        Ai[2] = -A[2] / J;
+        Ai[3] = A[0] / J;
+        return;
+    }
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / J;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) / J;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / J;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) / J;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / J;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) / J;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / J;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) / J;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / J;
+}
+
+static void transpose_d(int d, const double* A, double* At) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) At[j * d + i] = A[i * d + j];
+}
+
+static void matmul_d(int d, const double* A, const double* B, double* C) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += A[i * d + k] * B[k * d + j];
+            C[i * d + j] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* compressible Neo-Hookean law (density from the benchmark definition; the */
+/* paper's hyperelastic listing in Sec. 6.1 only sketches F = I + grad u)   */
+/* ------------------------------------------------------------------------ */
+double ora_nh_psi(int d, const double* F, double mu, double lam) {
+    double J = det_d(d, F);
+    if (!(J > 0.0)) return INFINITY;
+    double I1 = 0.0;
+    for (int k = 0; k < d * d; ++k) I1 += F[k] * F[k];
+    if (d == 2) I1 += 1.0; /* plane strain: F33 = 1 */
+    double lnJ = log(J);
+    return 0.5 * mu * (I1 - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ;
+}
+
+/* Magnitude of the density's individual terms, mu/2 I1 + mu |ln J| +
+ * lam/2 (ln J)^2: the scale of the roundoff made when psi is evaluated as
+ * written (psi itself can be many orders smaller near F = I).  The line
+ * search uses it to decide when an energy difference is below roundoff. */
+static double nh_term_scale(int d, const double* F, double mu, double lam) {
+    double J = det_d(d, F);
+    if (!(J > 0.0)) return 0.0;
+    double I1 = 0.0;
+    for (int k = 0; k < d * d; ++k) I1 += F[k] * F[k];
+    if (d == 2) I1 += 1.0;
+    double lnJ = log(J);
+    return 0.5 * mu * I1 + mu * fabs(lnJ) + 0.5 * lam * lnJ * lnJ;
+}
+
+/* P = mu (F - F^-T) + lam ln J F^-T */
+void ora_nh_P(int d, const double* F, double mu, double lam, double* P) {
+    double Fi[9], FiT[9];
+    inv_d(d, F, Fi);
+    transpose_d(d, Fi, FiT);
+    double lnJ = log(det_d(d, F));
+    for (int k = 0; k < d * d; ++k) P[k] = mu * (F[k] - FiT[k]) + lam * lnJ * FiT[k];
+}
+
+/* dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T */
+void ora_nh_dP(int d, const double* F, const double* dF, double mu, double lam, double* dP) {
+    double Fi[9] = {0}, FiT[9] = {0}, dFT[9] = {0}, T1[9] = {0}, T2[9] = {0}, A[9] = {0};
+    inv_d(d, F, Fi);
+    transpose_d(d, Fi, FiT);
+    transpose_d(d, dF, dFT);
+    double lnJ = log(det_d(d, F));
+    matmul_d(d, FiT, dFT, T1);
+    matmul_d(d, T1, FiT, T2); /* F^-T dF^T F^-T */
+    matmul_d(d, Fi, dF, A);   /* F^-1 dF */
+    double trA = 0.0;
+    for (int i = 0; i < d; ++i) trA += A[i * d + i];
+    for (int k = 0; k < d * d; ++k)
+        dP[k] = mu * dF[k] + (mu - lam * lnJ) * T2[k] + lam * trA * FiT[k];
+}
+
+/* ------------------------------------------------------------------------ */
+/* isoparametric geometry (Eq. 2: w_q det J^e(xi_q); grad N = J^-T grad N^)  */
+/* ------------------------------------------------------------------------ */
+static const int HEXSGN[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                 {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+/* reference gradients dN_a/dxi_j at quadrature point q; returns weight w_q */
+static double ref_grad(int etype, int q, double* gN /* [n_en][d] */) {
+    if (etype == 0) {
+        const double g[3][2] = {{-1, -1}, {1, 0}, {0, 1}};
+        memcpy(gN, g, sizeof g);
+        return 0.5;
+    }
+    if (etype == 1) {
+        const double g[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        memcpy(gN, g, sizeof g);
+        return 1.0 / 6.0;
+    }
+    /* 2x2x2 Gauss-Legendre point q = qi + 2 qj + 4 qk, coordinates +-1/sqrt(3) */
+    const double g = 1.0 / sqrt(3.0);
+    double xi[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+    for (int a = 0; a < 8; ++a) {
+        double f[3];
+        for (int j = 0; j < 3; ++j) f[j] = 1.0 + HEXSGN[a][j] * xi[j];
+        gN[a * 3 + 0] = 0.125 * HEXSGN[a][0] * f[1] * f[2];
+        gN[a * 3 + 1] = 0.125 * HEXSGN[a][1] * f[0] * f[2];
+        gN[a * 3 + 2] = 0.125 * HEXSGN[a][2] * f[0] * f[1];
+    }
+    return 1.0;
+}
+
+double ora_geometry(int etype, const double* Xe, int q, double* gradN, double* detJ_out) {
+    int d = ora_dim(etype), ne = ora_n_en(etype);
+    double gN[MAXEN * MAXD];
+    double w = ref_grad(etype, q, gN);
+    double J[9] = {0}, Ji[9];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < ne; ++a) s += Xe[a * d + i] * gN[a * d + j];
+            J[i * d + j] = s;
+        }
+    double detJ = det_d(d, J);
+    inv_d(d, J, Ji);
+    for (int a = 0; a < ne; ++a)
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) s += Ji[j * d + i] * gN[a * d + j];
+            gradN[a * d + i] = s;
+        }
+    if (detJ_out) *detJ_out = detJ;
+    return w * detJ;
+}
+
+/* gather element coordinates and a nodal field */
+static void gather(int d, int ne, const int32_t* c, const double* src, double* dst) {
+    for (int a = 0; a < ne; ++a)
+        for (int i = 0; i < d; ++i) dst[a * d + i] = src[(int64_t)c[a] * d + i];
+}
+
+/* F = I + sum_a u_a (x) gradN_a  (Algorithm 1, field gradient) */
+static void def_grad(int d, int ne, const double* ue, const double* gradN, double* F) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int a = 0; a < ne; ++a) s += ue[a * d + i] * gradN[a * d + j];
+            F[i * d + j] = s;
+        }
+}
+
+static void grad_field(int d, int ne, const double* ve, const double* gradN, double* G) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < ne; ++a) s += ve[a * d + i] * gradN[a * d + j];
+            G[i * d + j] = s;
+        }
+}
+
+static int finite_vec(int64_t n, const double* x) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(x[i])) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* energy (Eq. 2, Algorithm 1)                                              */
+/* ------------------------------------------------------------------------ */
+double ora_energy(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                  const int32_t* conn, const double* mu, const double* lam,
+                  const double* u, double* psi_e, double* abs_sum, int* status) {
+    int d = ora_dim(etype), ne = ora_n_en(etype), nq = ora_n_qp(etype);
+    int st = finite_vec(n_nodes * d, u) ? 0 : 4;
+    double sum = 0.0, comp = 0.0, asum = 0.0;
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t* c = conn + e * ne;
+        double Xe[MAXEN * MAXD], ue[MAXEN * MAXD], gN[MAXEN * MAXD], F[9];
+        gather(d, ne, c, X, Xe);
+        gather(d, ne, c, u, ue);
+        double pe = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
+            def_grad(d, ne, ue, gN, F);
+            pe += ora_nh_psi(d, F, mu[e], lam[e]) * wdJ;
+            asum += nh_term_scale(d, F, mu[e], lam[e]) * fabs(wdJ);
+        }
+        if (isinf(pe) && st == 0) st = 3;
+        if (psi_e) psi_e[e] = pe;
+        /* Neumaier summation */
+        double t = sum + pe;
+        if (fabs(sum) >= fabs(pe))
+            comp += (sum - t) + pe;
+        else
+            comp += (pe - t) + sum;
+        sum = t;
+    }
+    if (abs_sum) *abs_sum = asum;
+    if (status) *status = st;
+    if (st == 3) return INFINITY;
+    return sum + comp;
+}
+
+/* ------------------------------------------------------------------------ */
+/* residual r = grad Psi (Eq. 1): r_a += w detJ P gradN_a                   */
+/* ------------------------------------------------------------------------ */
+void ora_residual(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                  const int32_t* conn, const double* mu, const double* lam,
+                  const double* u, const uint8_t* mask, int mask_out, double* r,
+                  int* status) {
+    int d = ora_dim(etype), ne = ora_n_en(etype), nq = ora_n_qp(etype);
+    int st = finite_vec(n_nodes * d, u) ? 0 : 4;
+    memset(r, 0, sizeof(double) * n_nodes * d);
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t* c = conn + e * ne;
+        double Xe[MAXEN * MAXD], ue[MAXEN * MAXD], gN[MAXEN * MAXD], F[9], P[9];
+        gather(d, ne, c, X, Xe);
+        gather(d, ne, c, u, ue);
+        for (int q = 0; q < nq; ++q) {
+            double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
+            def_grad(d, ne, ue, gN, F);
+            if (!(det_d(d, F) > 0.0) && st == 0) st = 3;
+            ora_nh_P(d, F, mu[e], lam[e], P);
+            for (int a = 0; a < ne; ++a)
+                for (int i = 0; i < d; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < d; ++j) s += P[i * d + j] * gN[a * d + j];
+                    r[(int64_t)c[a] * d + i] += wdJ * s;
+                }
+        }
+    }
+    if (mask && mask_out)
+        for (int64_t k = 0; k < n_nodes * d; ++k)
+            if (mask[k]) r[k] = 0.0;
+    if (status) *status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hessian-vector product K v (Eq. 3): y_a += w detJ dP(dF) gradN_a         */
+/* ------------------------------------------------------------------------ */
+void ora_hvp(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+             const int32_t* conn, const double* mu, const double* lam,
+             const double* u, const double* v, const uint8_t* mask, int mask_in,
+             int mask_out, double* y, int* status) {
+    int d = ora_dim(etype), ne = ora_n_en(etype), nq = ora_n_qp(etype);
+    int64_t nd = n_nodes * d;
+    int st = (finite_vec(nd, u) && finite_vec(nd, v)) ? 0 : 4;
+    double* vm = (double*)malloc(sizeof(double) * nd);
+    for (int64_t k = 0; k < nd; ++k) vm[k] = (mask && mask_in && mask[k]) ? 0.0 : v[k];
+    memset(y, 0, sizeof(double) * nd);
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t* c = conn + e * ne;
+        double Xe[MAXEN * MAXD], ue[MAXEN * MAXD], ve[MAXEN * MAXD], gN[MAXEN * MAXD];
+        double F[9], dF[9], dP[9];
+        gather(d, ne, c, X, Xe);
+        gather(d, ne, c, u, ue);
+        gather(d, ne, c, vm, ve);
+        for (int q = 0; q < nq; ++q) {
+            double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
+            def_grad(d, ne, ue, gN, F);
+            if (!(det_d(d, F) > 0.0) && st == 0) st = 3;
+            grad_field(d, ne, ve, gN, dF);
+            ora_nh_dP(d, F, dF, mu[e], lam[e], dP);
+            for (int a = 0; a < ne; ++a)
+                for (int i = 0; i < d; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < d; ++j) s += dP[i * d + j] * gN[a * d + j];
+                    y[(int64_t)c[a] * d + i] += wdJ * s;
+                }
+        }
+    }
+    if (mask && mask_out)
+        for (int64_t k = 0; k < nd; ++k)
+            if (mask[k]) y[k] = 0.0;
+    free(vm);
+    if (status) *status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* nodal diagonal blocks K_ii: column k of the block is the HVP response at */
+/* node i to a unit vector e_k placed at node i (taken element by element)  */
+/* ------------------------------------------------------------------------ */
+void ora_block_diag(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                    const int32_t* conn, const double* mu, const double* lam,
+                    const double* u, const uint8_t* mask, double* D, int* status) {
+    int d = ora_dim(etype), ne = ora_n_en(etype), nq = ora_n_qp(etype);
+    int st = finite_vec(n_nodes * d, u) ? 0 : 4;
+    memset(D, 0, sizeof(double) * n_nodes * d * d);
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t* c = conn + e * ne;
+        double Xe[MAXEN * MAXD], ue[MAXEN * MAXD], gN[MAXEN * MAXD], F[9], dF[9], dP[9];
+        gather(d, ne, c, X, Xe);
+        gather(d, ne, c, u, ue);
+        for (int q = 0; q < nq; ++q) {
+            double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
+            def_grad(d, ne, ue, gN, F);
+            if (!(det_d(d, F) > 0.0) && st == 0) st = 3;
+            for (int a = 0; a < ne; ++a)
+                for (int k = 0; k < d; ++k) {
+                    /* dF = e_k (x) gradN_a */
+                    for (int i = 0; i < d; ++i)
+                        for (int j = 0; j < d; ++j) dF[i * d + j] = (i == k) ? gN[a * d + j] : 0.0;
+                    ora_nh_dP(d, F, dF, mu[e], lam[e], dP);
+                    for (int i = 0; i < d; ++i) {
+                        double s = 0.0;
+                        for (int j = 0; j < d; ++j) s += dP[i * d + j] * gN[a * d + j];
+                        D[(int64_t)c[a] * d * d + i * d + k] += wdJ * s;
+                    }
+                }
+        }
+    }
+    if (mask)
+        for (int64_t n = 0; n < n_nodes; ++n)
+            for (int k = 0; k < d; ++k)
+                if (mask[n * d + k])
+                    for (int j = 0; j < d; ++j) {
+                        D[n * d * d + k * d + j] = (j == k) ? 1.0 : 0.0;
+                        D[n * d * d + j * d + k] = (j == k) ? 1.0 : 0.0;
+                    }
+    if (status) *status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* parameter VJP: dP/dmu = F - F^-T, dP/dlam = ln J F^-T                    */
+/* ------------------------------------------------------------------------ */
+void ora_param_vjp(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                   const int32_t* conn, const double* mu, const double* lam,
+                   const double* u, const double* a, double* g_mu, double* g_lam,
+                   int* status) {
+    (void)mu;
+    (void)lam;
+    int d = ora_dim(etype), ne = ora_n_en(etype), nq = ora_n_qp(etype);
+    int st = finite_vec(n_nodes * d, u) ? 0 : 4;
+    for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t* c = conn + e * ne;
+        double Xe[MAXEN * MAXD], ue[MAXEN * MAXD], ae[MAXEN * MAXD], gN[MAXEN * MAXD];
+        double F[9], Fi[9], FiT[9];
+        gather(d, ne, c, X, Xe);
+        gather(d, ne, c, u, ue);
+        gather(d, ne, c, a, ae);
+        double gm = 0.0, gl = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
+            def_grad(d, ne, ue, gN, F);
+            double J = det_d(d, F);
+            if (!(J > 0.0) && st == 0) st = 3;
+            inv_d(d, F, Fi);
+            transpose_d(d, Fi, FiT);
+            double lnJ = log(J);
+            for (int b = 0; b < ne; ++b)
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j) {
+                        gm += wdJ * ae[b * d + i] * (F[i * d + j] - FiT[i * d + j]) * gN[b * d + j];
+                        gl += wdJ * ae[b * d + i] * lnJ * FiT[i * d + j] * gN[b * d + j];
+                    }
+        }
+        g_mu[e] = gm;
+        g_lam[e] = gl;
+    }
+    if (status) *status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Newton-CG load stepping                                                  */
+/*                                                                          */
+/* The paper solves the nonlinear problems with matrix-free Newton-Krylov   */
+/* iterations built on the residual and its JVP (Sec. 6.3.1, 6.6); it does  */
+/* not fix the details, so this routine fixes one algorithm that the GPU    */
+/* driver follows step for step:                                            */
+/*  1. du_c = (s - s_prev) ubar on prescribed DOFs.                         */
+/*  2. predictor: t = M K(u) (I-M) du_c, r0 = ||t||; solve M K M du_f = -t  */
+/*     by PCG to relative tolerance 1e-2; u += du_c + du_f.                 */
+/*  3. Newton: r = M grad Psi(u); stop when ||r|| <= rtol r0; PCG on        */
+/*     M K M d = -r from 0 with tolerance eta = min(eta_max, sqrt(||r||/r0))*/
+/*     (first-iteration negative curvature -> d = -Pr, later -> current d); */
+/*     backtracking Armijo on Psi with a roundoff guard that accepts when   */
+/*     |dPsi| <= 16 eps S and ||r|| decreases, S = sum over quadrature      */
+/*     points of w detJ (mu/2 I1 + mu |ln J| + lam/2 ln^2 J); u += alpha d. */
+/*  4. an inverted predictor, a failed line search or 50 Newton iterations  */
+/*     restore u and bisect the load increment (at most 5 levels).          */
+/* The preconditioner is block Jacobi: the inverse of each nodal diagonal   */
+/* block K_ii via its Cholesky factor.  Dot products are plain FP64 sums.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int etype, d;
+    int64_t nn, ne, nd;
+    const double *X, *mu, *lam, *ubar;
+    const int32_t* conn;
+    const uint8_t* mask;
+    const ora_newton_opts* o;
+    ora_newton_stats* st;
+    double *r, *t, *d_, *x, *res, *z, *p, *q, *Minv, *ut, *rt, *D;
+} ctx_t;
+
+static double dotv(int64_t n, const double* a, const double* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* block-Jacobi: Minv_i = D_i^-1 from the Cholesky factor D_i = L L^T */
+static int build_block_jacobi(ctx_t* c, const double* u) {
+    int d = c->d, stt;
+    ora_block_diag(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, c->mask, c->D, &stt);
+    for (int64_t n = 0; n < c->nn; ++n) {
+        const double* A = c->D + n * d * d;
+        double L[9] = {0}, Li[9] = {0};
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double s = A[i * d + j];
+                for (int k = 0; k < j; ++k) s -= L[i * d + k] * L[j * d + k];
+                if (i == j) {
+                    if (!(s > 0.0)) return 5;
+                    L[i * d + i] = sqrt(s);
+                } else {
+                    L[i * d + j] = s / L[j * d + j];
+                }
+            }
+        /* Li = L^-1 by forward substitution */
+        for (int j = 0; j < d; ++j) {
+            for (int i = 0; i < d; ++i) {
+                double s = (i == j) ? 1.0 : 0.0;
+                for (int k = 0; k < i; ++k) s -= L[i * d + k] * Li[k * d + j];
+                Li[i * d + j] = s / L[i * d + i];
+            }
+        }
+        /* Minv = Li^T Li */
+        double* Mi = c->Minv + n * d * d;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) s += Li[k * d + i] * Li[k * d + j];
+                Mi[i * d + j] = s;
+            }
+    }
+    return 0;
+}
+
+static void apply_prec(ctx_t* c, const double* in, double* out) {
+    int d = c->d;
+    for (int64_t n = 0; n < c->nn; ++n)
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) s += c->Minv[n * d * d + i * d + j] * in[n * d + j];
+            out[n * d + i] = s;
+        }
+}
+
+static void hvp_masked(ctx_t* c, const double* u, const double* v, double* y) {
+    int stt;
+    ora_hvp(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, v, c->mask, 1, 1, y, &stt);
+}
+
+/* PCG for M K M x = b from x = 0, stop at ||res|| <= tol_abs.  Returns the
+ * number of HVPs; sets *neg if non-positive curvature stopped it. */
+static int pcg(ctx_t* c, const double* u, const double* b, double tol_abs, int cg_max,
+               double* x) {
+    int64_t nd = c->nd;
+    memset(x, 0, sizeof(double) * nd);
+    memcpy(c->res, b, sizeof(double) * nd);
+    apply_prec(c, c->res, c->z);
+    memcpy(c->p, c->z, sizeof(double) * nd);
+    double rz = dotv(nd, c->res, c->z);
+    if (sqrt(dotv(nd, c->res, c->res)) <= tol_abs) return 0;
+    int k = 0;
+    for (; k < cg_max; ++k) {
+        hvp_masked(c, u, c->p, c->q);
+        double pq = dotv(nd, c->p, c->q);
+        if (!(pq > 0.0)) {
+            if (k == 0) memcpy(x, c->z, sizeof(double) * nd);
+            return k + 1;
+        }
+        double alpha = rz / pq;
+        for (int64_t i = 0; i < nd; ++i) {
+            x[i] += alpha * c->p[i];
+            c->res[i] -= alpha * c->q[i];
+        }
+        if (sqrt(dotv(nd, c->res, c->res)) <= tol_abs) return k + 1;
+        apply_prec(c, c->res, c->z);
+        double rz_new = dotv(nd, c->res, c->z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = 0; i < nd; ++i) c->p[i] = c->z[i] + beta * c->p[i];
+    }
+    return k;
+}
+
+/* one increment s0 -> s1 without bisection; returns 0 on success */
+static int increment(ctx_t* c, double s0, double s1, double* u) {
+    const ora_newton_opts* o = c->o;
+    int64_t nd = c->nd;
+    int stt;
+    int cg_max = o->cg_max > 0 ? o->cg_max : (int)(10 * nd);
+    /* 1-2: prescribed increment and linearised predictor */
+    for (int64_t i = 0; i < nd; ++i) c->d_[i] = c->mask[i] ? (s1 - s0) * c->ubar[i] : 0.0;
+    ora_hvp(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, c->d_, c->mask, 0, 1,
+            c->t, &stt);
+    if (stt) return 3;
+    double r0 = sqrt(dotv(nd, c->t, c->t));
+    if (r0 > 0.0) {
+        if (build_block_jacobi(c, u)) return 5;
+        for (int64_t i = 0; i < nd; ++i) c->t[i] = -c->t[i];
+        c->st->cg_iters += pcg(c, u, c->t, o->predictor_rtol * r0, cg_max, c->x);
+        for (int64_t i = 0; i < nd; ++i) u[i] += c->mask[i] ? c->d_[i] : c->x[i];
+    }
+    for (int64_t i = 0; i < nd; ++i)
+        if (c->mask[i]) u[i] = s1 * c->ubar[i];
+    double S;
+    double psi = ora_energy(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, NULL, &S,
+                            &stt);
+    if (stt == 3 || !isfinite(psi)) return 3;
+    ora_residual(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, c->mask, 1, c->r, &stt);
+    double rn = sqrt(dotv(nd, c->r, c->r));
+    if (!(r0 > 0.0)) r0 = rn;
+    c->st->r0_norm = r0;
+    /* 3: Newton loop */
+    for (int it = 0; it <= o->newton_max; ++it) {
+        c->st->r_norm = rn;
+        if (rn <= o->newton_rtol * r0) return 0;
+        if (it == o->newton_max) return 6;
+        c->st->newton_iters++;
+        double eta = sqrt(rn / r0);
+        if (eta > o->eta_max) eta = o->eta_max;
+        if (build_block_jacobi(c, u)) return 5;
+        for (int64_t i = 0; i < nd; ++i) c->t[i] = -c->r[i];
+        c->st->cg_iters += pcg(c, u, c->t, eta * rn, cg_max, c->x);
+        /* backtracking line search */
+        double g = dotv(nd, c->r, c->x);
+        double alpha = 1.0;
+        int ok = 0;
+        for (int ls = 0; ls <= o->ls_max; ++ls) {
+            for (int64_t i = 0; i < nd; ++i) c->ut[i] = u[i] + alpha * c->x[i];
+            double S_t;
+            double pt = ora_energy(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, c->ut,
+                                   NULL, &S_t, &stt);
+            if (isfinite(pt)) {
+                if (pt <= psi + o->armijo_c * alpha * g) {
+                    ok = 1;
+                } else if (fabs(pt - psi) <= 16.0 * o->ls_eps * S) {
+                    ora_residual(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, c->ut,
+                                 c->mask, 1, c->rt, &stt);
+                    if (sqrt(dotv(nd, c->rt, c->rt)) < rn) ok = 1;
+                }
+            }
+            if (ok) {
+                psi = pt;
+                S = S_t;
+                break;
+            }
+            alpha *= 0.5;
+            c->st->ls_halvings++;
+        }
+        if (!ok) return 7;
+        memcpy(u, c->ut, sizeof(double) * nd);
+        ora_residual(c->etype, c->nn, c->ne, c->X, c->conn, c->mu, c->lam, u, c->mask, 1, c->r,
+                     &stt);
+        rn = sqrt(dotv(nd, c->r, c->r));
+    }
+    return 6;
+}
+
+static int step_rec(ctx_t* c, double s0, double s1, double* u, int depth) {
+    double* save = (double*)malloc(sizeof(double) * c->nd);
+    memcpy(save, u, sizeof(double) * c->nd);
+    int rc = increment(c, s0, s1, u);
+    if (rc != 0 && depth < c->o->max_bisect) {
+        memcpy(u, save, sizeof(double) * c->nd);
+        c->st->bisections++;
+        double sm = 0.5 * (s0 + s1);
+        rc = step_rec(c, s0, sm, u, depth + 1);
+        if (rc == 0) rc = step_rec(c, sm, s1, u, depth + 1);
+    }
+    free(save);
+    return rc;
+}
+
+void ora_default_opts(ora_newton_opts* o) {
+    o->newton_rtol = 1e-8;
+    o->newton_max = 50;
+    o->eta_max = 0.1;
+    o->cg_max = 0;
+    o->predictor_rtol = 1e-2;
+    o->armijo_c = 1e-4;
+    o->ls_max = 20;
+    o->ls_eps = 2.220446049250313e-16;
+    o->max_bisect = 5;
+}
+
+int ora_load_step(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                  const int32_t* conn, const double* mu, const double* lam,
+                  const uint8_t* mask, const double* ubar, double s_prev, double s,
+                  double* u, const ora_newton_opts* opts, ora_newton_stats* stats) {
+    ora_newton_opts od;
+    if (!opts) {
+        ora_default_opts(&od);
+        opts = &od;
+    }
+    ctx_t c;
+    memset(&c, 0, sizeof c);
+    c.etype = etype;
+    c.d = ora_dim(etype);
+    c.nn = n_nodes;
+    c.ne = n_el;
+    c.nd = n_nodes * c.d;
+    c.X = X;
+    c.conn = conn;
+    c.mu = mu;
+    c.lam = lam;
+    c.mask = mask;
+    c.ubar = ubar;
+    c.o = opts;
+    c.st = stats;
+    memset(stats, 0, sizeof *stats);
+    double** bufs[] = {&c.r, &c.t, &c.d_, &c.x, &c.res, &c.z, &c.p, &c.q, &c.ut, &c.rt};
+    for (unsigned k = 0; k < sizeof bufs / sizeof bufs[0]; ++k)
+        *bufs[k] = (double*)calloc((size_t)c.nd, sizeof(double));
+    c.Minv = (double*)calloc((size_t)(n_nodes * c.d * c.d), sizeof(double));
+    c.D = (double*)calloc((size_t)(n_nodes * c.d * c.d), sizeof(double));
+    int rc = step_rec(&c, s_prev, s, u, 0);
+    stats->status = rc;
+    for (unsigned k = 0; k < sizeof bufs / sizeof bufs[0]; ++k) free(*bufs[k]);
+    free(c.Minv);
+    free(c.D);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-node MLP (learned block preconditioner), FP64                        */
+/* ------------------------------------------------------------------------ */
+static double silu(double t) { return t / (1.0 + exp(-t)); }
+static double dsilu(double t) {
+    double s = 1.0 / (1.0 + exp(-t));
+    return s * (1.0 + t * (1.0 - s));
+}
+
+static void dense(int din, int dout, const double* W, const double* b, const double* x,
+                  double* y) {
+    for (int o = 0; o < dout; ++o) {
+        double s = b[o];
+        for (int i = 0; i < din; ++i) s += W[o * din + i] * x[i];
+        y[o] = s;
+    }
+}
+
+void ora_mlp_forward(int n, int d_in, int h1, int h2, int d_out, const double* x,
+                     const double* W1, const double* b1, const double* W2,
+                     const double* b2, const double* W3, const double* b3,
+                     double* y) {
+    double* z1 = (double*)malloc(sizeof(double) * (h1 + h2));
+    double* z2 = z1 + h1;
+    for (int k = 0; k < n; ++k) {
+        dense(d_in, h1, W1, b1, x + (int64_t)k * d_in, z1);
+        for (int i = 0; i < h1; ++i) z1[i] = silu(z1[i]);
+        dense(h1, h2, W2, b2, z1, z2);
+        for (int i = 0; i < h2; ++i) z2[i] = silu(z2[i]);
+        dense(h2, d_out, W3, b3, z2, y + (int64_t)k * d_out);
+    }
+    free(z1);
+}
+
+void ora_mlp_backward(int n, int d_in, int h1, int h2, int d_out, const double* x,
+                      const double* W1, const double* b1, const double* W2,
+                      const double* b2, const double* W3, const double* b3,
+                      const double* gy, double* gW1, double* gb1, double* gW2,
+                      double* gb2, double* gW3, double* gb3, double* gx) {
+    (void)b3;
+    double* buf = (double*)malloc(sizeof(double) * 2 * (h1 + h2));
+    double *a1 = buf, *a2 = buf + h1, *g1 = buf + h1 + h2, *g2 = buf + 2 * h1 + h2;
+    for (int k = 0; k < n; ++k) {
+        const double* xk = x + (int64_t)k * d_in;
+        const double* gyk = gy + (int64_t)k * d_out;
+        dense(d_in, h1, W1, b1, xk, a1); /* pre-activations */
+        double h1v[256], h2v[256];
+        for (int i = 0; i < h1; ++i) h1v[i] = silu(a1[i]);
+        dense(h1, h2, W2, b2, h1v, a2);
+        for (int i = 0; i < h2; ++i) h2v[i] = silu(a2[i]);
+        /* layer 3 */
+        for (int o = 0; o < d_out; ++o) {
+            gb3[o] += gyk[o];
+            for (int i = 0; i < h2; ++i) gW3[o * h2 + i] += gyk[o] * h2v[i];
+        }
+        for (int i = 0; i < h2; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < d_out; ++o) s += W3[o * h2 + i] * gyk[o];
+            g2[i] = s * dsilu(a2[i]);
+        }
+        /* layer 2 */
+        for (int o = 0; o < h2; ++o) {
+            gb2[o] += g2[o];
+            for (int i = 0; i < h1; ++i) gW2[o * h1 + i] += g2[o] * h1v[i];
+        }
+        for (int i = 0; i < h1; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < h2; ++o) s += W2[o * h1 + i] * g2[o];
+            g1[i] = s * dsilu(a1[i]);
+        }
+        /* layer 1 */
+        for (int o = 0; o < h1; ++o) {
+            gb1[o] += g1[o];
+            for (int i = 0; i < d_in; ++i) gW1[o * d_in + i] += g1[o] * xk[i];
+        }
+        if (gx)
+            for (int i = 0; i < d_in; ++i) {
+                double s = 0.0;
+                for (int o = 0; o < h1; ++o) s += W1[o * d_in + i] * g1[o];
+                gx[(int64_t)k * d_in + i] = s;
+            }
+    }
+    free(buf);
+}
