@@ -1,0 +1,208 @@
+/*
+ * fem_b300.h -- C ABI of the B300 (sm_103a) energy-based FEM hot path.
+ *
+ * Method (arXiv 2602.12365, Sec. 2): the total potential of Eq. 2,
+ *     Psi_h(u) = sum_e sum_q psi(grad u_h^e(xi_q)) w_q det J^e(xi_q),
+ * is evaluated element by element (Algorithm 1: gather, field gradient,
+ * density, integrate, accumulate); the residual is its gradient and the
+ * tangent acts matrix-free as the directional derivative of the residual
+ * (Eq. 1 and Eq. 3).  The density is the compressible Neo-Hookean law
+ *     psi(F) = mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2,
+ * F = I + grad u, I1 = tr F^T F (+1 in 2D plane strain), J = det F.
+ * Dirichlet data follow the condensation of Sec. 6.1: prescribed components
+ * keep their values in u and are masked out of r and K.
+ *
+ * Conventions for every call below
+ *   - Vectors u, v, r, y, a are DEVICE pointers to flat [n_nodes * dim]
+ *     arrays, node-major and interleaved (node i, component k at i*dim+k),
+ *     of the dtype passed (FEM_F64: double, FEM_F32: float).  The caller owns
+ *     them; the library never frees or retains them after the call returns.
+ *   - Calls are asynchronous and ordered on the CUDA stream passed as `stream`
+ *     (a cudaStream_t, NULL = legacy default stream).  They allocate nothing
+ *     and never synchronise; each uses workspace owned by the mesh handle, so
+ *     calls on ONE handle must be ordered on one stream (two streams in
+ *     flight on the same handle race on that workspace).
+ *   - Kernels never trap.  Device-side conditions (some J <= 0, a non-finite
+ *     value) are OR-ed into the handle's status word; fem_sync_status()
+ *     synchronises the stream and returns and clears it.
+ *   - Every call returns a fem_status; FEM_OK means the work was enqueued.
+ *     fem_last_error() gives a message for the last failing call of the
+ *     calling thread.  No C++ exception crosses this boundary.
+ */
+#ifndef FEM_B300_H
+#define FEM_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_ERR_ARG = 1,           /* bad argument (null, size, enum)                */
+    FEM_ERR_CUDA = 2,          /* a CUDA runtime call failed                     */
+    FEM_ERR_INVERTED = 3,      /* some J <= 0: energy +inf, derivatives invalid   */
+    FEM_ERR_NONFINITE = 4,     /* NaN/Inf met in an input or a result            */
+    FEM_ERR_NOT_CONVERGED = 5, /* Newton or CG iteration cap reached             */
+    FEM_ERR_NEG_CURVATURE = 6, /* p^T K p <= 0 in CG                             */
+    FEM_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                   */
+    FEM_ERR_BADMESH = 8,       /* mesh does not fit the tiling limits            */
+    FEM_ERR_NOT_SPD = 9,       /* a nodal diagonal block is not positive definite */
+    FEM_ERR_LINESEARCH = 10    /* backtracking found no acceptable step          */
+} fem_status;
+
+typedef enum { FEM_TRI3 = 0, FEM_TET4 = 1, FEM_HEX8 = 2 } fem_elem_type;
+
+/* Arithmetic of a call: FEM_F64 everywhere, or FEM_F32 element kernels
+ * (reductions and energy sums stay FP64 in both). */
+typedef enum { FEM_F64 = 0, FEM_F32 = 1 } fem_dtype;
+
+/* Mesh precision: FEM_PREC_FP64 keeps FP64 geometry only; FEM_PREC_MIXED keeps
+ * FP32 geometry for the FEM_F32 kernels and FP64 geometry for FEM_F64 ones. */
+typedef enum { FEM_PREC_FP64 = 0, FEM_PREC_MIXED = 1 } fem_precision;
+
+/* Flags for fem_residual / fem_hvp */
+#define FEM_MASK_OUT 1u /* zero prescribed components of the result          */
+#define FEM_MASK_IN 2u  /* zero prescribed components of v before use (HVP)  */
+#define FEM_MASK_BOTH (FEM_MASK_IN | FEM_MASK_OUT)
+
+/* Status-word bits (fem_sync_status) */
+#define FEM_FLAG_INVERTED 1  /* some J <= 0 was met                   */
+#define FEM_FLAG_NONFINITE 2 /* some non-finite value was met          */
+#define FEM_FLAG_TIMEOUT 4   /* a bounded device wait gave up          */
+
+typedef struct fem_mesh fem_mesh; /* opaque; owns all device-side mesh data */
+
+/*
+ * Mesh description (all HOST pointers, read during fem_mesh_create only).
+ *   coords    [n_nodes * dim] double, reference positions X.
+ *   conn      [n_elems * n_en] int32, node ids; positive orientation.  n_en is
+ *             3 (P1 triangle, 1 point, w = 1/2), 4 (P1 tetrahedron, 1 point,
+ *             w = 1/6) or 8 (Q1 hexahedron, 2x2x2 Gauss, VTK vertex order).
+ *   mu, lambda [n_elems] double per-element Lame moduli, or NULL to use the
+ *             scalars mu0, lambda0 for every element.
+ *   dirichlet [n_nodes * dim] uint8, 1 = prescribed component; NULL = none.
+ *   tile_elems  elements per tile (0 = default: 1024 for P1, 512 for Q1).
+ */
+typedef struct {
+    int32_t elem_type; /* fem_elem_type */
+    int32_t precision; /* fem_precision */
+    int64_t n_nodes;
+    int64_t n_elems;
+    const double* coords;
+    const int32_t* conn;
+    const double* mu;
+    const double* lambda;
+    double mu0;
+    double lambda0;
+    const uint8_t* dirichlet;
+    int32_t tile_elems;
+    int32_t reserved;
+} fem_mesh_desc;
+
+/* Partition statistics (fem_mesh_get_info / fem_plan_partition). */
+typedef struct {
+    int64_t n_nodes, n_elems;
+    int32_t dim, n_en;
+    int32_t n_tiles;          /* level-1 parts, one CTA each                    */
+    int32_t max_tile_nodes;   /* largest local node set                         */
+    int64_t n_rounds;         /* level-2 colour classes (<= 32 disjoint elems)  */
+    int32_t max_rounds;       /* most rounds in one tile                        */
+    int32_t n_shared;         /* nodes touched by more than one tile            */
+    int64_t n_slots;          /* partial slots (sum over shared nodes of tiles) */
+    int64_t n_local_nodes;    /* sum over tiles of local nodes                  */
+    int64_t n_orphans;        /* nodes touched by no element                    */
+    double round_fill;        /* elements / (32 * rounds)                       */
+    int64_t device_bytes;     /* device memory held by the handle               */
+} fem_mesh_info;
+
+/*
+ * fem_mesh_create -- validate the mesh, partition it (tiles of spatially
+ * compact elements by recursive coordinate bisection; inside each tile,
+ * element colouring into rounds of at most 32 node-disjoint elements), and
+ * upload connectivity, precomputed P1 shape-function gradients and volumes
+ * (Alg. 1: gathered det J and grad N), coordinates (Q1), moduli and the
+ * Dirichlet mask.  Synchronous on `stream`.  Errors: FEM_ERR_ARG (null or
+ * inconsistent sizes, node id out of range), FEM_ERR_BADMESH (a tile needs
+ * more shared memory than the device offers, or a P1 element has det J <= 0),
+ * FEM_ERR_CUDA.  On error *out is NULL and nothing is leaked.
+ */
+fem_status fem_mesh_create(const fem_mesh_desc* desc, fem_mesh** out, void* stream);
+
+/* Release every device buffer of the handle (synchronises the device). */
+fem_status fem_mesh_destroy(fem_mesh* mesh);
+
+/* Fill *info (host) with the handle's partition statistics. */
+fem_status fem_mesh_get_info(const fem_mesh* mesh, fem_mesh_info* info);
+
+/*
+ * Host-only partition planner (no GPU needed): runs the same partitioner as
+ * fem_mesh_create and returns, per element (HOST arrays, length n_elems, any
+ * may be NULL), its tile, its global round (colour) id and its lane in the
+ * round, plus the statistics.  Used to check the colouring on a CPU.
+ */
+fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile,
+                              int64_t* elem_round, int32_t* elem_lane, fem_mesh_info* info);
+
+/*
+ * fem_energy -- Psi_h(u) (Eq. 2) with per-element densities in the call's
+ * dtype and an FP64 Neumaier-compensated, deterministic (fixed-order) sum.
+ *   out_dev  DEVICE double[4]: [0] Psi_h (+inf if some J <= 0), [1] the
+ *            roundoff scale S = sum_q w detJ (mu/2 I1 + mu |ln J| +
+ *            lam/2 ln^2 J) used by the line search, [2] the number of
+ *            quadrature points with J <= 0, [3] reserved (0).
+ */
+fem_status fem_energy(fem_mesh* mesh, int dtype, const void* u, double* out_dev, void* stream);
+
+/*
+ * fem_residual -- r = grad Psi_h(u) (Eq. 1): per element P = dpsi/dF =
+ * mu (F - F^-T) + lambda ln J F^-T, r_a += w detJ P grad N_a, scattered
+ * deterministically.  flags & FEM_MASK_OUT zeroes prescribed components.
+ * u and r must not alias.
+ */
+fem_status fem_residual(fem_mesh* mesh, int dtype, const void* u, void* r, unsigned flags,
+                        void* stream);
+
+/*
+ * fem_hvp -- y = Mo K(u) Mi v, the matrix-free tangent action (Eq. 3):
+ * dF = grad v, dP = mu dF + (mu - lambda ln J) F^-T dF^T F^-T +
+ * lambda tr(F^-1 dF) F^-T, y_a += w detJ dP grad N_a.  Mi / Mo are the
+ * Dirichlet masks selected by FEM_MASK_IN / FEM_MASK_OUT.
+ *   vKv_dev  DEVICE double* or NULL: receives (Mi v)^T K (Mi v) summed
+ *            element by element in FP64 in a fixed order.
+ * y must alias neither u nor v.
+ */
+fem_status fem_hvp(fem_mesh* mesh, int dtype, const void* u, const void* v, void* y,
+                   unsigned flags, double* vKv_dev, void* stream);
+
+/*
+ * fem_block_diag -- nodal diagonal blocks D_i = K_ii(u) (dim x dim, row
+ * major, [n_nodes * dim * dim] of the call's dtype); rows/columns of
+ * prescribed components are replaced by the identity.  Per element and node
+ * a: K_aa = w detJ [mu |g0|^2 I + (mu - lambda ln J + lambda) g g^T] with
+ * g0 = grad N_a and g = F^-T grad N_a.
+ */
+fem_status fem_block_diag(fem_mesh* mesh, int dtype, const void* u, void* D, void* stream);
+
+/*
+ * fem_param_vjp -- per-element sensitivities of a^T r(u) to the moduli:
+ * g_mu[e] = a^T dr_e/dmu_e, g_lam[e] = a^T dr_e/dlambda_e (dP/dmu = F - F^-T,
+ * dP/dlambda = ln J F^-T).  g_mu, g_lam: DEVICE double[n_elems] in the
+ * caller's element order (either may be NULL).
+ */
+fem_status fem_param_vjp(fem_mesh* mesh, int dtype, const void* u, const void* a,
+                         double* g_mu, double* g_lam, void* stream);
+
+/* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
+ * *flags and clear it. */
+fem_status fem_sync_status(fem_mesh* mesh, void* stream, int32_t* flags);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* fem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_B300_H */

@@ -1,0 +1,542 @@
+// C ABI of the B300 FEM hot path: mesh handle, element kernels, status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fem_b300.h"
+#include "fem_kernels.cuh"
+#include "fem_plan.h"
+
+namespace {
+thread_local std::string g_err;
+
+fem_status fail(fem_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(FEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+}  // namespace
+
+struct fem_mesh {
+    fem::Plan plan;
+    fem_mesh_info info{};
+    int etype = 0, dim = 0, n_en = 0, precision = 0;
+    bool per_elem_mat = false;
+    double mu0 = 1.0, lam0 = 10.0;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    // plan on the device
+    int32_t* tile_round_ptr = nullptr;
+    int64_t* tile_node_ptr = nullptr;
+    int32_t* node_gid = nullptr;
+    int32_t* node_slot = nullptr;
+    uint8_t* round_nvalid = nullptr;
+    int32_t* round_elem = nullptr;
+    int32_t* slot_owner = nullptr;
+    int32_t* shared_gid = nullptr;
+    int64_t* shared_slot_ptr = nullptr;
+    int32_t* shared_count = nullptr;
+    int32_t* orphans = nullptr;
+    uint8_t* node_mask = nullptr;
+    // element records per precision (index 0: FP64, 1: FP32)
+    uint8_t* rec[2] = {nullptr, nullptr};
+    int64_t rec_bytes[2] = {0, 0};
+    int geom_off[2] = {0, 0};
+    int mat_off[2] = {-1, -1};
+    void* X[2] = {nullptr, nullptr};
+    // workspace
+    void* partial = nullptr;
+    double* tile_red = nullptr;
+    unsigned* tile_counter = nullptr;
+    int* status = nullptr;
+};
+
+namespace {
+
+template <typename T>
+fem_status upload(fem_mesh* m, T** dst, const T* src, size_t n, cudaStream_t st) {
+    size_t bytes = sizeof(T) * (n > 0 ? n : 1);
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, bytes));
+    m->allocs.push_back(p);
+    m->bytes += (int64_t)bytes;
+    if (src && n) CUDA_TRY(cudaMemcpyAsync(p, src, sizeof(T) * n, cudaMemcpyHostToDevice, st));
+    *dst = static_cast<T*>(p);
+    return FEM_OK;
+}
+
+fem_status zalloc(fem_mesh* m, void** dst, size_t bytes, cudaStream_t st) {
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, bytes > 0 ? bytes : 16));
+    m->allocs.push_back(p);
+    m->bytes += (int64_t)bytes;
+    CUDA_TRY(cudaMemsetAsync(p, 0, bytes > 0 ? bytes : 16, st));
+    *dst = p;
+    return FEM_OK;
+}
+
+void free_all(fem_mesh* m) {
+    for (void* p : m->allocs) cudaFree(p);
+    m->allocs.clear();
+}
+
+int dim_of(int et) { return et == 0 ? 2 : 3; }
+int nen_of(int et) { return et == 0 ? 3 : (et == 1 ? 4 : 8); }
+
+// P1 shape-function gradients and w det J from the vertex positions:
+// J = [X_1 - X_0, ..., X_D - X_0] (reference gradients of N_1..N_D are the
+// unit vectors), grad N_a = row a-1 of J^-1 for a >= 1, grad N_0 = -sum.
+bool p1_geometry(int D, const double* Xe, double (*g)[3], double* wdJ) {
+    double J[3][3] = {{0}};
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) J[i][j] = Xe[(j + 1) * D + i] - Xe[i];
+    double det, Ji[3][3];
+    if (D == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        Ji[0][0] = J[1][1] / det;
+        Ji[0][1] = -J[0][1] / det;
+        Ji[1][0] = -J[1][0] / det;
+        Ji[1][1] = J[0][0] / det;
+        *wdJ = det / 2.0;
+    } else {
+        double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        Ji[0][0] = c00 / det;
+        Ji[1][0] = c01 / det;
+        Ji[2][0] = c02 / det;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        *wdJ = det / 6.0;
+    }
+    if (!(det > 0.0)) return false;
+    for (int k = 0; k < D; ++k) g[0][k] = 0.0;
+    for (int a = 1; a <= D; ++a)
+        for (int k = 0; k < D; ++k) {
+            g[a][k] = Ji[a - 1][k];
+            g[0][k] -= Ji[a - 1][k];
+        }
+    return true;
+}
+
+// det J of a Q1 element at every Gauss point must be positive
+bool hex_positive(const double* Xe) {
+    for (int q = 0; q < 8; ++q) {
+        double J[3][3] = {{0}};
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) J[i][j] += Xe[a * 3 + i] * fem::hex_dN(a, q, j);
+        double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!(det > 0.0)) return false;
+    }
+    return true;
+}
+
+// Record of one round: u16 conn[32][PAD] | T geom[NG][32] | T mat[2][32]
+template <typename T>
+void pack_records(fem_mesh* m, const fem_mesh_desc* d, const std::vector<double>& geo,
+                  std::vector<uint8_t>& out, int pi) {
+    const fem::Plan& P = m->plan;
+    const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
+    const int conn_bytes = 2 * 32 * P.n_en_pad;
+    const int geom_bytes = (int)sizeof(T) * 32 * NG;
+    const int mat_bytes = m->per_elem_mat ? (int)sizeof(T) * 64 : 0;
+    const int64_t RB = conn_bytes + geom_bytes + mat_bytes;
+    m->rec_bytes[pi] = RB;
+    m->geom_off[pi] = conn_bytes;
+    m->mat_off[pi] = m->per_elem_mat ? conn_bytes + geom_bytes : -1;
+    const int64_t NR = P.n_rounds();
+    out.assign((size_t)(NR * RB), 0);
+    for (int64_t r = 0; r < NR; ++r) {
+        uint8_t* rec = out.data() + r * RB;
+        std::memcpy(rec, P.round_conn.data() + r * 32 * P.n_en_pad, conn_bytes);
+        T* geom = reinterpret_cast<T*>(rec + conn_bytes);
+        T* mat = reinterpret_cast<T*>(rec + conn_bytes + geom_bytes);
+        for (int l = 0; l < 32; ++l) {
+            const int32_t e = P.round_elem[r * 32 + l];
+            if (e < 0) continue;
+            for (int k = 0; k < NG; ++k) geom[k * 32 + l] = (T)geo[(size_t)e * NG + k];
+            if (m->per_elem_mat) {
+                mat[l] = (T)d->mu[e];
+                mat[32 + l] = (T)d->lambda[e];
+            }
+        }
+    }
+}
+
+
+using KFn = void (*)(const fem::KParams);
+
+template <int ET, typename T>
+KFn pick(int op) {
+    switch (op) {
+        case fem::OP_ENERGY: return fem::tile_kernel<ET, T, fem::OP_ENERGY>;
+        case fem::OP_RESIDUAL: return fem::tile_kernel<ET, T, fem::OP_RESIDUAL>;
+        case fem::OP_HVP: return fem::tile_kernel<ET, T, fem::OP_HVP>;
+        case fem::OP_BLOCKDIAG: return fem::tile_kernel<ET, T, fem::OP_BLOCKDIAG>;
+        default: return fem::tile_kernel<ET, T, fem::OP_PVJP>;
+    }
+}
+
+KFn kernel_for(int et, int dtype, int op) {
+    if (dtype == FEM_F64) {
+        if (et == 0) return pick<0, double>(op);
+        if (et == 1) return pick<1, double>(op);
+        return pick<2, double>(op);
+    }
+    if (et == 0) return pick<0, float>(op);
+    if (et == 1) return pick<1, float>(op);
+    return pick<2, float>(op);
+}
+
+int max_optin_smem() {
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 227 * 1024;
+    }
+    return v;
+}
+
+int worst_smem(int et, int nl, bool mixed) {
+    int w = 0;
+    for (int op = 0; op < 5; ++op) {
+        w = std::max(w, fem::smem_layout(et, 8, op, nl).total);
+        if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nl).total);
+    }
+    return w;
+}
+
+fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
+                  double* out_scalar, double* out_mu, double* out_lam, unsigned flags,
+                  cudaStream_t st) {
+    if (!m) return fail(FEM_ERR_ARG, "null mesh");
+    if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
+    if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");
+    const int pi = dtype == FEM_F64 ? 0 : 1;
+    const int tsize = dtype == FEM_F64 ? 8 : 4;
+    fem::KParams p{};
+    p.tile_round_ptr = m->tile_round_ptr;
+    p.tile_node_ptr = m->tile_node_ptr;
+    p.node_gid = m->node_gid;
+    p.node_slot = m->node_slot;
+    p.round_nvalid = m->round_nvalid;
+    p.round_elem = m->round_elem;
+    p.rec = m->rec[pi];
+    p.rec_bytes = m->rec_bytes[pi];
+    p.geom_off = m->geom_off[pi];
+    p.mat_off = m->mat_off[pi];
+    p.slot_owner = m->slot_owner;
+    p.shared_gid = m->shared_gid;
+    p.shared_slot_ptr = m->shared_slot_ptr;
+    p.shared_count = m->shared_count;
+    p.orphans = m->orphans;
+    p.n_orphans = (int)m->plan.orphans.size();
+    p.node_mask = m->node_mask;
+    p.X = m->X[pi];
+    p.n_tiles = m->plan.n_tiles();
+    p.mu0 = m->mu0;
+    p.lam0 = m->lam0;
+    p.partial = m->partial;
+    p.tile_red = m->tile_red;
+    p.tile_counter = m->tile_counter;
+    p.status = m->status;
+    p.u = u;
+    p.v = v;
+    p.out = out;
+    p.out_scalar = out_scalar;
+    p.out_mu = out_mu;
+    p.out_lam = out_lam;
+    p.flags = flags;
+    const int smem = fem::smem_layout(m->etype, tsize, op, m->plan.max_tile_nodes).total;
+    KFn fn = kernel_for(m->etype, dtype, op);
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    fn<<<p.n_tiles, fem::kThreads, smem, st>>>(p);
+    CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+fem_status plan_from_desc(const fem_mesh_desc* d, fem::Plan& plan, int tile_elems) {
+    if (!d) return fail(FEM_ERR_ARG, "null descriptor");
+    if (d->elem_type < 0 || d->elem_type > 2) return fail(FEM_ERR_ARG, "elem_type must be 0, 1 or 2");
+    if (d->n_nodes <= 0 || d->n_elems <= 0) return fail(FEM_ERR_ARG, "empty mesh");
+    if (!d->coords || !d->conn) return fail(FEM_ERR_ARG, "coords and conn are required");
+    if ((d->mu == nullptr) != (d->lambda == nullptr))
+        return fail(FEM_ERR_ARG, "mu and lambda must both be given or both be NULL");
+    fem::MeshInput in;
+    in.elem_type = d->elem_type;
+    in.dim = dim_of(d->elem_type);
+    in.n_en = nen_of(d->elem_type);
+    in.n_nodes = d->n_nodes;
+    in.n_el = d->n_elems;
+    in.X = d->coords;
+    in.conn = d->conn;
+    in.tile_elems = tile_elems;
+    std::string err = fem::build_plan(in, plan);
+    if (!err.empty()) return fail(err.find("out of range") != std::string::npos ? FEM_ERR_ARG : FEM_ERR_BADMESH, err);
+    return FEM_OK;
+}
+
+void fill_info(const fem::Plan& P, fem_mesh_info* info) {
+    std::memset(info, 0, sizeof *info);
+    info->n_nodes = P.n_nodes;
+    info->n_elems = P.n_el;
+    info->dim = P.dim;
+    info->n_en = P.n_en;
+    info->n_tiles = P.n_tiles();
+    info->max_tile_nodes = P.max_tile_nodes;
+    info->n_rounds = P.n_rounds();
+    info->max_rounds = P.max_rounds;
+    info->n_shared = (int32_t)P.shared_gid.size();
+    info->n_slots = P.n_slots();
+    info->n_local_nodes = (int64_t)P.node_gid.size();
+    info->n_orphans = (int64_t)P.orphans.size();
+    info->round_fill = P.n_rounds() ? (double)P.n_el / (32.0 * (double)P.n_rounds()) : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fem_last_error(void) { return g_err.c_str(); }
+
+fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile, int64_t* elem_round,
+                              int32_t* elem_lane, fem_mesh_info* info) {
+    fem::Plan P;
+    fem_status s = plan_from_desc(desc, P, desc ? desc->tile_elems : 0);
+    if (s != FEM_OK) return s;
+    for (int t = 0; t < P.n_tiles(); ++t)
+        for (int32_t r = P.tile_round_ptr[t]; r < P.tile_round_ptr[t + 1]; ++r)
+            for (int l = 0; l < P.round_nvalid[r]; ++l) {
+                int32_t e = P.round_elem[(int64_t)r * 32 + l];
+                if (elem_tile) elem_tile[e] = t;
+                if (elem_round) elem_round[e] = r;
+                if (elem_lane) elem_lane[e] = l;
+            }
+    if (info) fill_info(P, info);
+    return FEM_OK;
+}
+
+fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream) {
+    if (!out) return fail(FEM_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (!d) return fail(FEM_ERR_ARG, "null descriptor");
+    if (d->precision != FEM_PREC_FP64 && d->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "precision must be FEM_PREC_FP64 or FEM_PREC_MIXED");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fem_mesh* m = new fem_mesh();
+    m->etype = d->elem_type;
+    m->precision = d->precision;
+    m->dim = dim_of(d->elem_type);
+    m->n_en = nen_of(d->elem_type);
+    m->per_elem_mat = d->mu != nullptr;
+    m->mu0 = d->mu0;
+    m->lam0 = d->lambda0;
+    const bool mixed = d->precision == FEM_PREC_MIXED;
+    // plan; halve the tile until its shared memory fits the device
+    int tile = d->tile_elems;
+    fem_status s;
+    for (int attempt = 0;; ++attempt) {
+        s = plan_from_desc(d, m->plan, tile);
+        if (s != FEM_OK) {
+            delete m;
+            return s;
+        }
+        if (worst_smem(m->etype, m->plan.max_tile_nodes, mixed) <= max_optin_smem()) break;
+        tile = m->plan.tile_elems / 2;
+        if (tile < 32 || attempt > 6) {
+            delete m;
+            return fail(FEM_ERR_BADMESH, "a tile's nodes do not fit in shared memory");
+        }
+    }
+    const fem::Plan& P = m->plan;
+    const int D = m->dim, NEN = m->n_en;
+    const int64_t NE = d->n_elems, NN = d->n_nodes;
+
+    // per-element geometry (P1) and orientation checks
+    std::vector<double> geo;
+    const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
+    if (NG) {
+        geo.assign((size_t)NE * NG, 0.0);
+        double Xe[4 * 3], g[4][3], wdJ;
+        for (int64_t e = 0; e < NE; ++e) {
+            for (int a = 0; a < NEN; ++a)
+                for (int k = 0; k < D; ++k) Xe[a * D + k] = d->coords[(size_t)d->conn[e * NEN + a] * D + k];
+            if (!p1_geometry(D, Xe, g, &wdJ)) {
+                delete m;
+                return fail(FEM_ERR_BADMESH, "element " + std::to_string(e) + " has det J <= 0");
+            }
+            // the kernel takes the LAST vertex as reference: store grad N_0..N_{NEN-2}
+            for (int a = 0; a < NEN - 1; ++a)
+                for (int k = 0; k < D; ++k) geo[(size_t)e * NG + a * D + k] = g[a][k];
+            geo[(size_t)e * NG + NG - 1] = wdJ;
+        }
+    } else {
+        double Xe[24];
+        for (int64_t e = 0; e < NE; ++e) {
+            for (int a = 0; a < 8; ++a)
+                for (int k = 0; k < 3; ++k) Xe[a * 3 + k] = d->coords[(size_t)d->conn[e * 8 + a] * 3 + k];
+            if (!hex_positive(Xe)) {
+                delete m;
+                return fail(FEM_ERR_BADMESH, "hexahedron " + std::to_string(e) + " has det J <= 0");
+            }
+        }
+    }
+    std::vector<uint8_t> mask(NN, 0);
+    if (d->dirichlet)
+        for (int64_t n = 0; n < NN; ++n)
+            for (int k = 0; k < D; ++k)
+                if (d->dirichlet[n * D + k]) mask[n] |= (uint8_t)(1u << k);
+
+#define UP(dst, vec) \
+    if ((s = upload(m, &m->dst, (vec).data(), (vec).size(), st)) != FEM_OK) goto fail_out
+    UP(tile_round_ptr, P.tile_round_ptr);
+    UP(tile_node_ptr, P.tile_node_ptr);
+    UP(node_gid, P.node_gid);
+    UP(node_slot, P.node_slot);
+    UP(round_nvalid, P.round_nvalid);
+    UP(round_elem, P.round_elem);
+    UP(slot_owner, P.slot_owner);
+    UP(shared_gid, P.shared_gid);
+    UP(shared_slot_ptr, P.shared_slot_ptr);
+    UP(orphans, P.orphans);
+    UP(node_mask, mask);
+#undef UP
+    {
+        std::vector<uint8_t> recs;
+        for (int pi = 0; pi < 2; ++pi) {
+            if (pi == 1 && !mixed) break;
+            if (pi == 0)
+                pack_records<double>(m, d, geo, recs, 0);
+            else
+                pack_records<float>(m, d, geo, recs, 1);
+            if ((s = upload(m, &m->rec[pi], recs.data(), recs.size(), st)) != FEM_OK) goto fail_out;
+            if (m->etype == 2) {
+                if (pi == 0) {
+                    double* x = nullptr;
+                    if ((s = upload(m, &x, d->coords, (size_t)NN * 3, st)) != FEM_OK) goto fail_out;
+                    m->X[0] = x;
+                } else {
+                    std::vector<float> xf((size_t)NN * 3);
+                    for (size_t i = 0; i < xf.size(); ++i) xf[i] = (float)d->coords[i];
+                    float* x = nullptr;
+                    if ((s = upload(m, &x, xf.data(), xf.size(), st)) != FEM_OK) goto fail_out;
+                    m->X[1] = x;
+                }
+            }
+            // records are host temporaries: finish the copy before reuse
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                s = fail(FEM_ERR_CUDA, "cudaStreamSynchronize failed during upload");
+                goto fail_out;
+            }
+        }
+    }
+    {
+        void* p = nullptr;
+        const int aw = D == 2 ? 4 : 6;
+        if ((s = zalloc(m, &p, (size_t)std::max<int64_t>(P.n_slots(), 1) * aw * 8, st)) != FEM_OK) goto fail_out;
+        m->partial = p;
+        if ((s = zalloc(m, &p, (size_t)P.n_tiles() * 4 * 8, st)) != FEM_OK) goto fail_out;
+        m->tile_red = static_cast<double*>(p);
+        if ((s = zalloc(m, &p, 16, st)) != FEM_OK) goto fail_out;
+        m->tile_counter = static_cast<unsigned*>(p);
+        if ((s = zalloc(m, &p, 16, st)) != FEM_OK) goto fail_out;
+        m->status = static_cast<int*>(p);
+        if ((s = zalloc(m, &p, sizeof(int32_t) * std::max<size_t>(P.shared_gid.size(), 1), st)) != FEM_OK)
+            goto fail_out;
+        m->shared_count = static_cast<int32_t*>(p);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        s = fail(FEM_ERR_CUDA, "cudaStreamSynchronize failed after upload");
+        goto fail_out;
+    }
+    fill_info(P, &m->info);
+    m->info.device_bytes = m->bytes;
+    *out = m;
+    return FEM_OK;
+fail_out:
+    free_all(m);
+    delete m;
+    return s;
+}
+
+fem_status fem_mesh_destroy(fem_mesh* m) {
+    if (!m) return FEM_OK;
+    cudaDeviceSynchronize();
+    free_all(m);
+    delete m;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_get_info(const fem_mesh* m, fem_mesh_info* info) {
+    if (!m || !info) return fail(FEM_ERR_ARG, "null argument");
+    *info = m->info;
+    return FEM_OK;
+}
+
+fem_status fem_energy(fem_mesh* m, int dtype, const void* u, double* out_dev, void* stream) {
+    if (!u || !out_dev) return fail(FEM_ERR_ARG, "null u or output");
+    return launch(m, dtype, fem::OP_ENERGY, u, nullptr, nullptr, out_dev, nullptr, nullptr, 0,
+                  static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_residual(fem_mesh* m, int dtype, const void* u, void* r, unsigned flags, void* stream) {
+    if (!u || !r) return fail(FEM_ERR_ARG, "null u or r");
+    if (u == r) return fail(FEM_ERR_ARG, "u and r must not alias");
+    return launch(m, dtype, fem::OP_RESIDUAL, u, nullptr, r, nullptr, nullptr, nullptr, flags,
+                  static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_hvp(fem_mesh* m, int dtype, const void* u, const void* v, void* y, unsigned flags,
+                   double* vKv_dev, void* stream) {
+    if (!u || !v || !y) return fail(FEM_ERR_ARG, "null u, v or y");
+    if (y == u || y == v) return fail(FEM_ERR_ARG, "y must alias neither u nor v");
+    return launch(m, dtype, fem::OP_HVP, u, v, y, vKv_dev, nullptr, nullptr, flags,
+                  static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_block_diag(fem_mesh* m, int dtype, const void* u, void* D, void* stream) {
+    if (!u || !D) return fail(FEM_ERR_ARG, "null u or D");
+    return launch(m, dtype, fem::OP_BLOCKDIAG, u, nullptr, D, nullptr, nullptr, nullptr, 0,
+                  static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_param_vjp(fem_mesh* m, int dtype, const void* u, const void* a, double* g_mu,
+                         double* g_lam, void* stream) {
+    if (!u || !a) return fail(FEM_ERR_ARG, "null u or a");
+    return launch(m, dtype, fem::OP_PVJP, u, a, nullptr, nullptr, g_mu, g_lam, 0,
+                  static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_sync_status(fem_mesh* m, void* stream, int32_t* flags) {
+    if (!m || !flags) return fail(FEM_ERR_ARG, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *flags = h;
+    return FEM_OK;
+}
+
+}  // extern "C"

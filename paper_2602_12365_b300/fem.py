@@ -1,0 +1,168 @@
+"""Python face of the C ABI: a mesh handle and its element operators.
+
+PyTorch supplies device memory and the current CUDA stream; each method only
+marshals pointers and sizes into one C call.  Vectors are flat
+``[n_nodes * dim]`` CUDA tensors (float64 for FEM_F64 calls, float32 for
+FEM_F32 calls), node-major and interleaved.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return L.FEM_F64
+    if t.dtype == torch.float32:
+        return L.FEM_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def make_desc(elem_type, coords, conn, mu=None, lam=None, mu0=1.0, lam0=10.0, dirichlet=None,
+              precision="mixed", tile_elems=0):
+    """Build a MeshDesc plus the host arrays it points to (kept alive)."""
+    keep = {
+        "coords": np.ascontiguousarray(coords, dtype=np.float64),
+        "conn": np.ascontiguousarray(conn, dtype=np.int32),
+    }
+    if mu is not None:
+        keep["mu"] = np.ascontiguousarray(mu, dtype=np.float64)
+        keep["lam"] = np.ascontiguousarray(lam, dtype=np.float64)
+    if dirichlet is not None:
+        keep["dir"] = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    d = L.MeshDesc()
+    d.elem_type = int(elem_type)
+    d.precision = L.FEM_PREC_MIXED if precision == "mixed" else L.FEM_PREC_FP64
+    d.n_nodes = keep["coords"].shape[0]
+    d.n_elems = keep["conn"].shape[0]
+    d.coords = keep["coords"].ctypes.data
+    d.conn = keep["conn"].ctypes.data
+    d.mu = keep["mu"].ctypes.data if "mu" in keep else None
+    d.lam = keep["lam"].ctypes.data if "lam" in keep else None
+    d.mu0 = float(mu0)
+    d.lambda0 = float(lam0)
+    d.dirichlet = keep["dir"].ctypes.data if "dir" in keep else None
+    d.tile_elems = int(tile_elems)
+    return d, keep
+
+
+def plan_partition(elem_type, coords, conn, tile_elems=0):
+    """Host-only partition (no GPU): per element tile, round (colour), lane."""
+    d, keep = make_desc(elem_type, coords, conn, tile_elems=tile_elems)
+    ne = d.n_elems
+    tile = np.zeros(ne, np.int32)
+    rnd = np.zeros(ne, np.int64)
+    lane = np.zeros(ne, np.int32)
+    info = L.MeshInfo()
+    L.check(L.lib().fem_plan_partition(C.byref(d), tile.ctypes.data, rnd.ctypes.data,
+                                       lane.ctypes.data, C.byref(info)))
+    return tile, rnd, lane, info.as_dict()
+
+
+class Mesh:
+    """A mesh uploaded to the GPU (owns the C handle)."""
+
+    def __init__(self, elem_type, coords, conn, mu=None, lam=None, mu0=1.0, lam0=10.0,
+                 dirichlet=None, precision="mixed", tile_elems=0, stream=None):
+        d, keep = make_desc(elem_type, coords, conn, mu, lam, mu0, lam0, dirichlet, precision,
+                            tile_elems)
+        h = C.c_void_p()
+        L.check(L.lib().fem_mesh_create(C.byref(d), C.byref(h), _stream(stream)))
+        self._h = h
+        self.elem_type = int(elem_type)
+        self.dim = 2 if elem_type == 0 else 3
+        self.n_nodes = int(d.n_nodes)
+        self.n_el = int(d.n_elems)
+        self.precision = precision
+        self.mask = None
+        if dirichlet is not None:
+            self.mask = torch.as_tensor(keep["dir"].reshape(-1).astype(bool)).cuda()
+
+    @classmethod
+    def from_fixture(cls, m, precision="mixed", tile_elems=0):
+        return cls(m.elem_type, m.coords, m.conn, m.mu, m.lam, m.mu0, m.lam0, m.dirichlet,
+                   precision, tile_elems)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().fem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_dofs(self):
+        return self.n_nodes * self.dim
+
+    def info(self) -> dict:
+        i = L.MeshInfo()
+        L.check(L.lib().fem_mesh_get_info(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def _check_vec(self, *ts):
+        for t in ts:
+            if not (t.is_cuda and t.is_contiguous() and t.numel() == self.n_dofs):
+                raise ValueError("vectors must be contiguous CUDA tensors of n_nodes*dim entries")
+
+    # --- element operators -------------------------------------------------
+    def energy(self, u, out=None, stream=None):
+        """Device double[4]: Psi, roundoff scale S, #(J <= 0), 0."""
+        self._check_vec(u)
+        out = out if out is not None else torch.empty(4, dtype=torch.float64, device=u.device)
+        L.check(L.lib().fem_energy(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
+    def residual(self, u, mask_out=True, out=None, stream=None):
+        self._check_vec(u)
+        out = out if out is not None else torch.empty_like(u)
+        L.check(L.lib().fem_residual(self._h, _dtype_code(u), _ptr(u), _ptr(out),
+                                     L.FEM_MASK_OUT if mask_out else 0, _stream(stream)))
+        return out
+
+    def hvp(self, u, v, mask_in=True, mask_out=True, out=None, vkv=None, stream=None):
+        self._check_vec(u, v)
+        if u.dtype != v.dtype:
+            raise TypeError("u and v must have the same dtype")
+        out = out if out is not None else torch.empty_like(u)
+        flags = (L.FEM_MASK_IN if mask_in else 0) | (L.FEM_MASK_OUT if mask_out else 0)
+        L.check(L.lib().fem_hvp(self._h, _dtype_code(u), _ptr(u), _ptr(v), _ptr(out), flags,
+                                _ptr(vkv), _stream(stream)))
+        return out
+
+    def block_diag(self, u, out=None, stream=None):
+        self._check_vec(u)
+        out = out if out is not None else torch.empty(self.n_nodes * self.dim * self.dim,
+                                                      dtype=u.dtype, device=u.device)
+        L.check(L.lib().fem_block_diag(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
+    def param_vjp(self, u, a, stream=None):
+        self._check_vec(u, a)
+        gm = torch.empty(self.n_el, dtype=torch.float64, device=u.device)
+        gl = torch.empty(self.n_el, dtype=torch.float64, device=u.device)
+        L.check(L.lib().fem_param_vjp(self._h, _dtype_code(u), _ptr(u), _ptr(a), _ptr(gm), _ptr(gl),
+                                      _stream(stream)))
+        return gm, gl
+
+    def sync_status(self, stream=None) -> int:
+        f = C.c_int32(0)
+        L.check(L.lib().fem_sync_status(self._h, _stream(stream), C.byref(f)))
+        return f.value

@@ -1,0 +1,96 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point the
+header declares, and its host partitioner produces a valid two-level
+colouring (no GPU call is made)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2602_12365_b300 import build as B
+from paper_2602_12365_b300 import meshgen as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_2602_12365_b300 import _lib
+    return _lib
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"^\s*(?:fem_status|const char\s*\*)\s*(fem_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 10
+    so = C.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    assert set(lib.EXPORTED) >= names
+
+
+def test_bad_descriptor_is_rejected_without_gpu(lib):
+    from paper_2602_12365_b300.fem import make_desc
+    m = mg.tri_mesh(2)
+    conn = m.conn.copy()
+    conn[0, 0] = 10_000
+    d, keep = make_desc(m.elem_type, m.coords, conn)
+    info = lib.MeshInfo()
+    st = lib.lib().fem_plan_partition(C.byref(d), None, None, None, C.byref(info))
+    assert st == 1  # FEM_ERR_ARG
+    assert b"out of range" in lib.lib().fem_last_error()
+    st = lib.lib().fem_plan_partition(None, None, None, None, None)
+    assert st == 1
+
+
+@pytest.mark.parametrize("kind,n,tile", [("tri", 24, 128), ("tet", 6, 200), ("tet", 9, 0),
+                                         ("hex", 7, 64), ("hex", 5, 0)])
+def test_two_level_colouring_is_valid(lib, kind, n, tile):
+    from paper_2602_12365_b300.fem import plan_partition
+    m = {"tri": lambda: mg.tri_mesh(n), "tet": lambda: mg.tet_mesh(n, jitter_seed=1),
+         "hex": lambda: mg.hex_mesh(n)}[kind]()
+    tile_of, rnd, lane, info = plan_partition(m.elem_type, m.coords, m.conn, tile)
+    ne = m.n_el
+    # every element exactly once: (round, lane) pairs are unique
+    key = rnd * 32 + lane
+    assert len(np.unique(key)) == ne
+    assert np.all((lane >= 0) & (lane < 32))
+    # no node repeats within a round (the element colouring)
+    order = np.argsort(rnd, kind="stable")
+    r_sorted = rnd[order]
+    bounds = np.flatnonzero(np.diff(r_sorted)) + 1
+    for grp in np.split(order, bounds):
+        nodes = m.conn[grp].ravel()
+        assert len(np.unique(nodes)) == nodes.size
+        assert len(np.unique(tile_of[grp])) == 1   # a round lies inside one tile
+    # tiles are at most the requested size and cover everything
+    T = tile if tile > 0 else (512 if kind == "hex" else 1024)
+    assert np.bincount(tile_of).max() <= T
+    assert info["n_tiles"] == tile_of.max() + 1
+    # shared-node bookkeeping: slots = sum over nodes of (#tiles touching) for shared nodes
+    node_tiles = {}
+    for e in range(ne):
+        for nd in m.conn[e]:
+            node_tiles.setdefault(int(nd), set()).add(int(tile_of[e]))
+    counts = np.array([len(s) for s in node_tiles.values()])
+    assert info["n_shared"] == int((counts > 1).sum())
+    assert info["n_slots"] == int(counts[counts > 1].sum())
+    assert 0 < info["round_fill"] <= 1.0
+
+
+def test_plan_is_deterministic(lib):
+    from paper_2602_12365_b300.fem import plan_partition
+    m = mg.tet_mesh(6, jitter_seed=3)
+    a = plan_partition(m.elem_type, m.coords, m.conn, 128)
+    b = plan_partition(m.elem_type, m.coords, m.conn, 128)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
