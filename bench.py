@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark: residual + HVP throughput of the energy-based FEM hot path.
+
+Workload: 64^3 cube of Kuhn tetrahedra (1,572,864 P1 elements, 274,625 nodes,
+interior nodes jittered by U(-0.1h, 0.1h) from seed 0), compressible
+Neo-Hookean mu = 1, lambda = 10, base clamped and top prescribed; FP32
+element kernels with FP64 reductions.  One step = one residual + one HVP at
+the BC-consistent state u (load factor 0.5: affine part plus a 0.02 sine
+bump) along v ~ N(0, 1) on free DOFs.  Metric: elements per second of the
+pair, N_el / (t_residual + t_hvp), in GElem/s.
+
+L2 (126 MB) is flushed before every timed step by writing a 256 MB buffer;
+each step is timed with CUDA events on the stream the kernels run on.
+`--impl reference` times the FP64 CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic bytes per element for the tet workload (FP32): element stream
+# conn 16 + 3 grad N 36 + w detJ 4 = 56 B, plus nodal vectors at 0.1746 nodes
+# per element: residual u 12 + r 12 + mask 1 = 25 B, HVP u 12 + v 12 + y 12 +
+# mask 1 = 37 B (each read or written once).
+B_RES_PER_EL = 60.4
+B_HVP_PER_EL = 62.5
+WORKLOAD = "tet64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="cells per side")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_12365_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_tag):
+    """DRAM bytes per call from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_call")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fem_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, parts in rows:
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(n):
+    from paper_2602_12365_b300 import meshgen as mg
+    m = mg.workload_tet(n, seed=0)
+    u = mg.smooth_state(m, 0.5).ravel()
+    v = mg.random_direction(m, 1).ravel()
+    return m, u, v
+
+
+def config_dict(m, step, extra=None):
+    d = {"workload": f"{WORKLOAD}: 3D P1 Kuhn tetrahedra on a {m.n}^3 unit cube, "
+                     f"{m.n_el} elements, {m.n_nodes} nodes, interior jitter 0.1h (seed 0), "
+                     "Neo-Hookean mu=1 lambda=10, base clamped, top prescribed; "
+                     "u = BC-consistent state at load factor 0.5, v ~ N(0,1) on free DOFs",
+         "n_el": m.n_el, "n_nodes": m.n_nodes, "step": step,
+         "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def cpu_oracle_rate(m, u, v, reps=2):
+    """Oracle residual + HVP on the whole workload, single thread."""
+    import oracle
+    om = oracle.OracleMesh.from_mesh(m)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        om.residual(u)
+        om.hvp(u, v)
+        ts.append(time.perf_counter() - t0)
+    t = min(ts)
+    return m.n_el / t / 1e9, t
+
+
+def run_reference(args):
+    world, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    import oracle
+    m, u, v = workload(args.n)
+    # each step: oracle residual + HVP over a fixed contiguous quarter of the
+    # elements (a bounded sample of the same workload)
+    ne = m.n_el // 4
+    sub = oracle.OracleMesh(m.elem_type, m.coords, m.conn[:ne], m.mu_e()[:ne], m.lam_e()[:ne],
+                            m.dirichlet)
+    for _ in range(args.warmup):
+        sub.residual(u)
+        sub.hvp(u, v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sub.residual(u)
+        sub.hvp(u, v)
+    dt = time.perf_counter() - t0
+    val = ne * args.steps / dt / 1e9
+    sample = f"oracle residual+HVP over the first {ne} of {m.n_el} elements, {args.steps} steps"
+    line = {"impl": "reference", "metric": "residual+HVP GElem/s", "value": val, "unit": "GElem/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(m, "1 residual + 1 HVP (FP64 CPU oracle, 1 thread)",
+                                  {"sample": sample}),
+            "cpu_baseline": {"value": val, "unit": "GElem/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GElem/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2602_12365_b300 import fem
+    from paper_2602_12365_b300.fem import Mesh
+
+    m, u, v = workload(args.n)
+    gm = Mesh.from_fixture(m, precision="mixed")
+    info = gm.info()
+    ut = torch.as_tensor(u, dtype=torch.float32, device=dev)
+    vt = torch.as_tensor(v, dtype=torch.float32, device=dev)
+    r = torch.empty_like(ut)
+    y = torch.empty_like(ut)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        gm.residual(ut, out=r)
+        gm.hvp(ut, vt, out=y)
+    torch.cuda.synchronize()
+    assert gm.sync_status() == 0, "device status flagged during warm-up"
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            gm.residual(ut, out=r)
+            ev[k][1].record(stream)
+            gm.hvp(ut, vt, out=y)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(world)
+    t_res = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps  # ms
+    t_hvp = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    t_step = max_over_ranks(t_res + t_hvp, world, dev)
+    t_res = max_over_ranks(t_res, world, dev)
+    t_hvp = max_over_ranks(t_hvp, world, dev)
+    flags = gm.sync_status()
+
+    # end to end through the C ABI with host buffers: H2D of u, v; D2H of r, y
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.as_tensor(u, dtype=torch.float32).pin_memory()
+        vh = torch.as_tensor(v, dtype=torch.float32).pin_memory()
+        rh = torch.empty_like(uh).pin_memory()
+        yh = torch.empty_like(uh).pin_memory()
+        ud = torch.empty_like(ut)
+        vd = torch.empty_like(ut)
+
+        def e2e_step():
+            ud.copy_(uh, non_blocking=True)
+            vd.copy_(vh, non_blocking=True)
+            gm.residual(ud, out=r)
+            gm.hvp(ud, vd, out=y)
+            rh.copy_(r, non_blocking=True)
+            yh.copy_(y, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        t_e2e = max_over_ranks(tot / args.steps, world, dev)
+        nb = ut.numel() * 4
+        e2e = {"value": world * m.n_el / (t_e2e * 1e-3) / 1e9, "unit": "GElem/s",
+               "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb,
+               "ms_per_step": t_e2e}
+
+    peak, peak_kind = measured_peaks()
+    dominant = "hvp" if t_hvp >= t_res else "residual"
+    t_dom = t_hvp if dominant == "hvp" else t_res
+    b_dom = (B_HVP_PER_EL if dominant == "hvp" else B_RES_PER_EL) * m.n_el
+    achieved = b_dom / (t_dom * 1e-3) / 1e9
+    tr = traffic_for(f"{WORKLOAD}_{dominant}_f32")
+    value = world * m.n_el / (t_step * 1e-3) / 1e9
+    launches = fem.KERNELS_PER_CALL
+    line = {
+        "metric": "residual+HVP GElem/s", "value": value, "unit": "GElem/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": config_dict(m, "1 residual + 1 HVP (FP32 element kernels, FP64 reductions)",
+                              {"tiles": info["n_tiles"], "rounds": info["n_rounds"],
+                               "round_fill": round(info["round_fill"], 4)}),
+        "residual_us": t_res * 1e3, "hvp_us": t_hvp * 1e3,
+        "residual_gelem_s": m.n_el / (t_res * 1e-3) / 1e9,
+        "hvp_gelem_s": m.n_el / (t_hvp * 1e-3) / 1e9,
+        "pair_hbm_frac": (B_RES_PER_EL + B_HVP_PER_EL) * m.n_el / ((t_res + t_hvp) * 1e-3) / 1e9 / peak,
+        "roofline": {"bound": "hbm", "kernel": f"fem_{dominant} (tet4, f32)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "bytes_per_el": B_HVP_PER_EL if dominant == "hvp" else B_RES_PER_EL,
+                     "timed": "whole C-ABI call (all its kernels), CUDA events on its stream",
+                     "traffic": tr},
+        "gpu_launches": (launches["residual"] + launches["hvp"]) * args.steps,
+        "device_flags": flags,
+        "wall_s_timed_region": wall,
+    }
+    line["clocks"] = clk.summary()
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, t = cpu_oracle_rate(m, u, v)
+        line["cpu_baseline"] = {"value": rate, "unit": "GElem/s", "cores": 1, "kind": "oracle",
+                                "sample": f"whole workload, one residual + one HVP, best of 2 "
+                                          f"({t:.2f} s each)"}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -14,6 +14,10 @@ import torch
 
 from . import _lib as L
 
+# CUDA kernels each C-ABI call launches (tile kernel, plus the finalize kernel
+# that sums the tile-shared nodes where there is one)
+KERNELS_PER_CALL = {"energy": 1, "residual": 1, "hvp": 1, "block_diag": 1, "param_vjp": 1}
+
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
