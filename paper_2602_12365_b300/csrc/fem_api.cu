@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fem_b300.h"
@@ -45,14 +48,13 @@ struct fem_mesh {
     int32_t* slot_owner = nullptr;
     int32_t* shared_gid = nullptr;
     int64_t* shared_slot_ptr = nullptr;
-    int32_t* shared_count = nullptr;
     int32_t* orphans = nullptr;
     uint8_t* node_mask = nullptr;
     // element records per precision (index 0: FP64, 1: FP32)
     uint8_t* rec[2] = {nullptr, nullptr};
     int64_t rec_bytes[2] = {0, 0};
-    int geom_off[2] = {0, 0};
-    int mat_off[2] = {-1, -1};
+    int conn_bytes = 0;
+    int stride = 0;
     void* X[2] = {nullptr, nullptr};
     // workspace
     void* partial = nullptr;
@@ -149,38 +151,43 @@ bool hex_positive(const double* Xe) {
     return true;
 }
 
-// Record of one round: u16 conn[32][PAD] | T geom[NG][32] | T mat[2][32]
+// Record of one round (one bulk copy): u16 conn[32][PAD] | T elem[32][stride],
+// elem = (grad N_0 .. grad N_{NEN-2}, w det J | mu, lambda), stride even.
+int elem_stride(int etype, bool mat) {
+    const int NG = etype == 0 ? 5 : (etype == 1 ? 10 : 0);
+    const int n = NG + (mat ? 2 : 0);
+    return (n + 1) & ~1;
+}
+
 template <typename T>
 void pack_records(fem_mesh* m, const fem_mesh_desc* d, const std::vector<double>& geo,
                   std::vector<uint8_t>& out, int pi) {
     const fem::Plan& P = m->plan;
     const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
     const int conn_bytes = 2 * 32 * P.n_en_pad;
-    const int geom_bytes = (int)sizeof(T) * 32 * NG;
-    const int mat_bytes = m->per_elem_mat ? (int)sizeof(T) * 64 : 0;
-    const int64_t RB = conn_bytes + geom_bytes + mat_bytes;
+    const int stride = elem_stride(m->etype, m->per_elem_mat);
+    const int64_t RB = conn_bytes + (int64_t)sizeof(T) * 32 * stride;
     m->rec_bytes[pi] = RB;
-    m->geom_off[pi] = conn_bytes;
-    m->mat_off[pi] = m->per_elem_mat ? conn_bytes + geom_bytes : -1;
+    m->conn_bytes = conn_bytes;
+    m->stride = stride;
     const int64_t NR = P.n_rounds();
     out.assign((size_t)(NR * RB), 0);
     for (int64_t r = 0; r < NR; ++r) {
         uint8_t* rec = out.data() + r * RB;
         std::memcpy(rec, P.round_conn.data() + r * 32 * P.n_en_pad, conn_bytes);
-        T* geom = reinterpret_cast<T*>(rec + conn_bytes);
-        T* mat = reinterpret_cast<T*>(rec + conn_bytes + geom_bytes);
+        T* el = reinterpret_cast<T*>(rec + conn_bytes);
         for (int l = 0; l < 32; ++l) {
             const int32_t e = P.round_elem[r * 32 + l];
             if (e < 0) continue;
-            for (int k = 0; k < NG; ++k) geom[k * 32 + l] = (T)geo[(size_t)e * NG + k];
+            T* x = el + l * stride;
+            for (int k = 0; k < NG; ++k) x[k] = (T)geo[(size_t)e * NG + k];
             if (m->per_elem_mat) {
-                mat[l] = (T)d->mu[e];
-                mat[32 + l] = (T)d->lambda[e];
+                x[NG] = (T)d->mu[e];
+                x[NG + 1] = (T)d->lambda[e];
             }
         }
     }
 }
-
 
 using KFn = void (*)(const fem::KParams);
 
@@ -217,13 +224,32 @@ int max_optin_smem() {
     return v;
 }
 
-int worst_smem(int et, int nl, bool mixed) {
+int record_bytes(int et, bool mat, int tsize) {
+    const int pad = et == 2 ? 8 : 4;
+    return 2 * 32 * pad + tsize * 32 * elem_stride(et, mat);
+}
+
+int worst_smem(int et, int nl, bool mixed, bool mat) {
     int w = 0;
     for (int op = 0; op < 5; ++op) {
-        w = std::max(w, fem::smem_layout(et, 8, op, nl).total);
-        if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nl).total);
+        w = std::max(w, fem::smem_layout(et, 8, op, nl, record_bytes(et, mat, 8)).total);
+        if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nl, record_bytes(et, mat, 4)).total);
     }
     return w;
+}
+
+template <int D, typename T>
+KFn pick_fin(int op) {
+    switch (op) {
+        case fem::OP_RESIDUAL: return fem::finalize_kernel<D, T, fem::OP_RESIDUAL>;
+        case fem::OP_HVP: return fem::finalize_kernel<D, T, fem::OP_HVP>;
+        default: return fem::finalize_kernel<D, T, fem::OP_BLOCKDIAG>;
+    }
+}
+
+KFn finalize_for(int dim, int dtype, int op) {
+    if (dtype == FEM_F64) return dim == 2 ? pick_fin<2, double>(op) : pick_fin<3, double>(op);
+    return dim == 2 ? pick_fin<2, float>(op) : pick_fin<3, float>(op);
 }
 
 fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
@@ -243,13 +269,14 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.round_nvalid = m->round_nvalid;
     p.round_elem = m->round_elem;
     p.rec = m->rec[pi];
-    p.rec_bytes = m->rec_bytes[pi];
-    p.geom_off = m->geom_off[pi];
-    p.mat_off = m->mat_off[pi];
+    p.rec_bytes = (int)m->rec_bytes[pi];
+    p.conn_bytes = m->conn_bytes;
+    p.stride = m->stride;
+    p.has_mat = m->per_elem_mat ? 1 : 0;
     p.slot_owner = m->slot_owner;
     p.shared_gid = m->shared_gid;
     p.shared_slot_ptr = m->shared_slot_ptr;
-    p.shared_count = m->shared_count;
+    p.n_shared = (int)m->plan.shared_gid.size();
     p.orphans = m->orphans;
     p.n_orphans = (int)m->plan.orphans.size();
     p.node_mask = m->node_mask;
@@ -268,11 +295,41 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_mu = out_mu;
     p.out_lam = out_lam;
     p.flags = flags;
-    const int smem = fem::smem_layout(m->etype, tsize, op, m->plan.max_tile_nodes).total;
+    const int smem =
+        fem::smem_layout(m->etype, tsize, op, m->plan.max_tile_nodes, (int)m->rec_bytes[pi]).total;
     KFn fn = kernel_for(m->etype, dtype, op);
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    {
+        // raise the dynamic shared-memory limit once per (device, kernel)
+        static std::mutex mu;
+        static std::map<std::pair<int, const void*>, int> set_to;
+        int dev = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(mu);
+        auto key = std::make_pair(dev, reinterpret_cast<const void*>(fn));
+        auto it = set_to.find(key);
+        if (it == set_to.end() || it->second < smem) {
+            CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            set_to[key] = smem;
+        }
+    }
     fn<<<p.n_tiles, fem::kThreads, smem, st>>>(p);
     CUDA_TRY(cudaGetLastError());
+    if (op == fem::OP_RESIDUAL || op == fem::OP_HVP || op == fem::OP_BLOCKDIAG) {
+        // shared nodes: programmatic dependent launch, so the launch overlaps
+        // the tile kernel's tail; the kernel waits on griddepcontrol.wait
+        const int total = p.n_shared + p.n_orphans;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::max(1, (total + fem::kFinThreads - 1) / fem::kFinThreads));
+        cfg.blockDim = dim3(fem::kFinThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CUDA_TRY(cudaLaunchKernelEx(&cfg, finalize_for(m->dim, dtype, op), p));
+    }
     return FEM_OK;
 }
 
@@ -362,7 +419,7 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
             delete m;
             return s;
         }
-        if (worst_smem(m->etype, m->plan.max_tile_nodes, mixed) <= max_optin_smem()) break;
+        if (worst_smem(m->etype, m->plan.max_tile_nodes, mixed, m->per_elem_mat) <= max_optin_smem()) break;
         tile = m->plan.tile_elems / 2;
         if (tile < 32 || attempt > 6) {
             delete m;
@@ -462,9 +519,6 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
         m->tile_counter = static_cast<unsigned*>(p);
         if ((s = zalloc(m, &p, 16, st)) != FEM_OK) goto fail_out;
         m->status = static_cast<int*>(p);
-        if ((s = zalloc(m, &p, sizeof(int32_t) * std::max<size_t>(P.shared_gid.size(), 1), st)) != FEM_OK)
-            goto fail_out;
-        m->shared_count = static_cast<int32_t*>(p);
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         s = fail(FEM_ERR_CUDA, "cudaStreamSynchronize failed after upload");

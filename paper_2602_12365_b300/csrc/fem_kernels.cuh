@@ -1,68 +1,88 @@
 // Tile kernels of the energy-based FEM hot path (sm_103a).
 //
-// One CTA owns one tile (see fem_plan.h).  It stages the tile's nodal data
-// in shared memory, runs the tile's rounds (warp w takes rounds w, w+4, ...;
-// one element per lane; the elements of a round share no node), accumulates
-// nodal results into its warp's private shared-memory copy, combines the
-// copies in warp order and writes: private nodes directly, shared nodes as
-// a partial into their fixed slot.  The last tile to finish a shared node
-// (an integer arrival counter per node) sums its slots in slot order.  Every
-// sum therefore has a fixed order: results are bitwise reproducible and no
-// floating-point atomic is used.
+// Per element (Algorithm 1 of arXiv 2602.12365): gather the nodal values,
+// form H = grad u = sum_a u_a (x) grad N_a and F = I + H, evaluate the
+// Neo-Hookean density / stress / tangent action (fem_material.cuh), multiply
+// by w_q det J and scatter.  P1 elements read precomputed grad N_a and
+// w det J from their round record; Q1 hexahedra rebuild J from the staged
+// nodal coordinates at each of the 2x2x2 Gauss points.
 //
-// Per element (Algorithm 1 of arXiv 2602.12365): gather nodal values, form
-// H = grad u = sum_a u_a (x) grad N_a and F = I + H, evaluate the
-// compressible Neo-Hookean density / stress / tangent action, multiply by
-// w_q det J and scatter.  P1 elements read precomputed grad N_a and w det J
-// from a per-round record; Q1 hexahedra rebuild J from the staged nodal
-// coordinates at each of the 2x2x2 Gauss points.
-//
-// FP32 accuracy: J - 1 is formed from the invariants of H and F^-T - I from
-// the cofactor identity cof(I + H) = (1 + tr H) I - H^T + cof(H), so no
-// quantity near 1 is ever subtracted from 1; differences u_a - u_ref are taken
-// before the gradient sums.
+// Work decomposition (fem_plan.h): one CTA of kWarps warps owns one tile.
+//   prologue  bulk copies (TMA engine) of the first round records of every
+//             warp start; the tile's nodal u (v, X), node ids and partial
+//             slots are gathered into shared memory; accumulators zeroed.
+//   rounds    warp w runs a contiguous range of the tile's rounds, one
+//             element per lane (two elements per lane, packed in FP32x2
+//             pairs, for FP32 P1 calls), and accumulates into its own
+//             shared-memory copy.  The elements of one round share no node,
+//             so lanes never collide; rounds of one warp are applied in
+//             order.  Records stream through a per-warp ring of kStages
+//             stages filled by cp.async.bulk and guarded by mbarriers (every
+//             wait is bounded and reports FEM_FLAG_TIMEOUT).
+//   epilogue  the warp copies are summed in warp order; nodes private to the
+//             tile are written, nodes shared with other tiles go to their
+//             fixed partial slot.
+// finalize_kernel (launched with programmatic dependent launch) sums each
+// shared node's slots in slot (= tile) order.  Every sum has a fixed order,
+// so results are bitwise reproducible and no floating-point atomic is used.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
+
+#include "fem_material.cuh"
+#include "fem_vec.cuh"
 
 namespace fem {
 
 constexpr int kWarps = 4;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kSpinLimit = 1 << 22;
+constexpr int kStages = 3;           // ring stages per warp
+constexpr int kSpinLimit = 1 << 20;  // bounded mbarrier waits
+constexpr int kFinThreads = 256;
 
 enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4 };
 
 template <int ET>
 struct ElemT;
 template <>
-struct ElemT<0> {  // P1 triangle, plane strain
-    static constexpr int D = 2, NEN = 3, NQ = 1, PAD = 4, NG = 5, VW = 2;
+struct ElemT<0> {  // P1 triangle, plane strain, 1 point
+    static constexpr int D = 2, NEN = 3, PAD = 4, NG = 5, VW = 2;
 };
 template <>
-struct ElemT<1> {  // P1 tetrahedron
-    static constexpr int D = 3, NEN = 4, NQ = 1, PAD = 4, NG = 10, VW = 4;
+struct ElemT<1> {  // P1 tetrahedron, 1 point
+    static constexpr int D = 3, NEN = 4, PAD = 4, NG = 10, VW = 4;
 };
 template <>
 struct ElemT<2> {  // Q1 hexahedron, 2x2x2 Gauss
-    static constexpr int D = 3, NEN = 8, NQ = 8, PAD = 8, NG = 0, VW = 4;
+    static constexpr int D = 3, NEN = 8, PAD = 8, NG = 0, VW = 4;
 };
 
+// rounds per warp iteration: FP32 P1 calls pack two rounds into FP32x2 pairs
+__host__ __device__ constexpr int rounds_per_iter(int et, int tsize) {
+    return (et != 2 && tsize == 4) ? 2 : 1;
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory layout (bytes), identical on host and device
+// ---------------------------------------------------------------------------
 struct SmemLayout {
-    int off_u, off_v, off_x, off_acc, off_mask, off_red, total, aw;
+    int off_u, off_v, off_x, off_acc, acc_bytes, off_mask, off_gid, off_slot, off_red, off_ring,
+        off_bar, total, aw, stage_bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int align128(int x) { return (x + 127) & ~127; }
 
-__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nl) {
+__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nl, int rec_bytes) {
     SmemLayout L;
-    int D = et == 0 ? 2 : 3;
-    int VW = D == 2 ? 2 : 4;
-    int vec = VW * tsize;
+    const int D = et == 0 ? 2 : 3;
+    const int VW = D == 2 ? 2 : 4;
+    const int vec = VW * tsize;
     L.aw = (op == OP_BLOCKDIAG) ? (D == 2 ? 4 : 6) : VW;
-    bool need_v = (op == OP_HVP || op == OP_PVJP);
-    bool need_acc = (op == OP_RESIDUAL || op == OP_HVP || op == OP_BLOCKDIAG);
+    const bool need_v = (op == OP_HVP || op == OP_PVJP);
+    const bool need_acc = (op == OP_RESIDUAL || op == OP_HVP || op == OP_BLOCKDIAG);
     int o = 0;
     L.off_u = o;
     o = align16(o + nl * vec);
@@ -71,12 +91,22 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     L.off_x = o;
     if (et == 2) o = align16(o + nl * vec);
     L.off_acc = o;
-    if (need_acc) o = align16(o + kWarps * nl * L.aw * tsize);
+    L.acc_bytes = need_acc ? align16(kWarps * nl * L.aw * tsize) : 0;
+    o += L.acc_bytes;
+    L.off_gid = o;
+    o = align16(o + nl * 4);
+    L.off_slot = o;
+    o = align16(o + nl * 4);
     L.off_mask = o;
     o = align16(o + nl);
     L.off_red = o;
     o = align16(o + kWarps * 4 * 8 + 16);
-    L.total = o;
+    L.stage_bytes = rounds_per_iter(et, tsize) * rec_bytes;
+    L.off_ring = o = align128(o);
+    o += kWarps * kStages * L.stage_bytes;
+    L.off_bar = o = align16(o);
+    o += kWarps * kStages * 8;
+    L.total = align16(o);
     return L;
 }
 
@@ -88,14 +118,17 @@ struct KParams {
     const int32_t* node_slot;
     const uint8_t* round_nvalid;
     const int32_t* round_elem;
+    // round records: u16 conn[32][PAD] | T elem[32][stride] (elem: grad N_0..
+    // grad N_{NEN-2}, w det J for P1; then mu, lambda when has_mat)
     const uint8_t* rec;
-    int64_t rec_bytes;
-    int geom_off;
-    int mat_off;  // -1: uniform moduli
+    int rec_bytes;
+    int conn_bytes;
+    int stride;
+    int has_mat;
     const int32_t* slot_owner;
     const int32_t* shared_gid;
     const int64_t* shared_slot_ptr;
-    int32_t* shared_count;
+    int n_shared;
     const int32_t* orphans;
     int n_orphans;
     const uint8_t* node_mask;
@@ -118,21 +151,65 @@ struct KParams {
 };
 
 // ---------------------------------------------------------------------------
-// scalar helpers
+// bulk copies (TMA engine), mbarriers and dependent launch, by inline PTX
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
-__device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// arm the barrier for `bytes` and start one bulk copy global -> shared
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the copy did not land within the limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory vectors
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
 
-template <typename T>
-__device__ __forceinline__ T ldg_(const T* p) {
-    return __ldg(p);
-}
-
-// Nodal vectors in shared memory: VW-wide, 16-byte aligned for 3D FP32.
 template <int VW, typename T>
 __device__ __forceinline__ void lds_vec(const T* base, int i, T* out) {
     if constexpr (VW == 4 && sizeof(T) == 4) {
@@ -140,6 +217,7 @@ __device__ __forceinline__ void lds_vec(const T* base, int i, T* out) {
         out[0] = t.x;
         out[1] = t.y;
         out[2] = t.z;
+        out[3] = t.w;
     } else if constexpr (VW == 2 && sizeof(T) == 4) {
         float2 t = reinterpret_cast<const float2*>(base)[i];
         out[0] = t.x;
@@ -150,6 +228,7 @@ __device__ __forceinline__ void lds_vec(const T* base, int i, T* out) {
         out[0] = a.x;
         out[1] = a.y;
         out[2] = b.x;
+        out[3] = b.y;
     } else {
         double2 a = reinterpret_cast<const double2*>(base)[i];
         out[0] = a.x;
@@ -160,144 +239,97 @@ __device__ __forceinline__ void lds_vec(const T* base, int i, T* out) {
 template <int VW, typename T>
 __device__ __forceinline__ void sts_vec(T* base, int i, const T* in) {
     if constexpr (VW == 4 && sizeof(T) == 4) {
-        reinterpret_cast<float4*>(base)[i] = make_float4(in[0], in[1], in[2], 0.f);
+        reinterpret_cast<float4*>(base)[i] = make_float4(in[0], in[1], in[2], in[3]);
     } else if constexpr (VW == 2 && sizeof(T) == 4) {
         reinterpret_cast<float2*>(base)[i] = make_float2(in[0], in[1]);
     } else if constexpr (VW == 4) {
         reinterpret_cast<double2*>(base)[2 * i] = make_double2(in[0], in[1]);
-        reinterpret_cast<double2*>(base)[2 * i + 1] = make_double2(in[2], 0.0);
+        reinterpret_cast<double2*>(base)[2 * i + 1] = make_double2(in[2], in[3]);
     } else {
         reinterpret_cast<double2*>(base)[i] = make_double2(in[0], in[1]);
     }
 }
 
-// acc[i] += f (read-modify-write of one nodal accumulator)
-template <int VW, int D, typename T>
-__device__ __forceinline__ void rmw_vec(T* base, int i, const T* f) {
-    T cur[4];
-    lds_vec<VW, T>(base, i, cur);
+// lane's element data from a round record in shared memory
+template <typename T, int N>
+__device__ __forceinline__ void lds_elem(const T* src, int stride, T (&dst)[N]) {
+    if constexpr (sizeof(T) == 4) {
+        if (stride % 4 == 0) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) cur[k] += f[k];
-    sts_vec<VW, T>(base, i, cur);
+            for (int k = 0; k < (N + 3) / 4; ++k) {
+                float4 t = reinterpret_cast<const float4*>(src)[k];
+                if (4 * k + 0 < N) dst[4 * k + 0] = t.x;
+                if (4 * k + 1 < N) dst[4 * k + 1] = t.y;
+                if (4 * k + 2 < N) dst[4 * k + 2] = t.z;
+                if (4 * k + 3 < N) dst[4 * k + 3] = t.w;
+            }
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < (N + 1) / 2; ++k) {
+            float2 t = reinterpret_cast<const float2*>(src)[k];
+            if (2 * k + 0 < N) dst[2 * k + 0] = t.x;
+            if (2 * k + 1 < N) dst[2 * k + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < (N + 1) / 2; ++k) {
+            double2 t = reinterpret_cast<const double2*>(src)[k];
+            if (2 * k + 0 < N) dst[2 * k + 0] = t.x;
+            if (2 * k + 1 < N) dst[2 * k + 1] = t.y;
+        }
+    }
 }
 
-// ---------------------------------------------------------------------------
-// Neo-Hookean kinematics from H = grad u
-// ---------------------------------------------------------------------------
-template <int D, typename T>
-struct Kin {
-    T G[D][D];  // F^-T - I
-    T lnJ;
-    T trH, HH;  // tr H, H:H
-    bool ok;    // J > 0
+// one half of a lane's work: an element of a round record
+template <int ET, typename T>
+struct Half {
+    static constexpr int NEN = ElemT<ET>::NEN, NG = ElemT<ET>::NG;
+    int cn[NEN];
+    T ed[NG + 2];  // geometry, mu, lambda
 };
 
-template <int D, typename T>
-__device__ __forceinline__ void kinematics(const T (&H)[D][D], Kin<D, T>& k) {
-    k.trH = 0;
-    k.HH = 0;
+template <int ET, typename T>
+__device__ __forceinline__ void read_half(const uint8_t* rec, int lane, bool valid, const KParams& p,
+                                          Half<ET, T>& h) {
+    using E = ElemT<ET>;
+    if (!valid) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        k.trH += H[i][i];
+        for (int a = 0; a < E::NEN; ++a) h.cn[a] = 0;
 #pragma unroll
-        for (int j = 0; j < D; ++j) k.HH = fma(H[i][j], H[i][j], k.HH);
+        for (int j = 0; j < E::NG + 2; ++j) h.ed[j] = T(0);
+        return;
     }
-    if constexpr (D == 2) {
-        T detH = H[0][0] * H[1][1] - H[0][1] * H[1][0];
-        T Jm1 = k.trH + detH;
-        T J = T(1) + Jm1;
-        k.ok = J > T(0);
-        T rJ = rcp_(J);
-        // cof(F) - J I = -det(H) I - H^T
-        k.G[0][0] = (-detH - H[0][0]) * rJ;
-        k.G[0][1] = -H[1][0] * rJ;
-        k.G[1][0] = -H[0][1] * rJ;
-        k.G[1][1] = (-detH - H[1][1]) * rJ;
-        k.lnJ = k.ok ? log1p_(Jm1) : T(0);
+    if constexpr (E::PAD == 4) {
+        uint2 w = reinterpret_cast<const uint2*>(rec)[lane];
+        h.cn[0] = w.x & 0xffff;
+        h.cn[1] = w.x >> 16;
+        h.cn[2] = w.y & 0xffff;
+        if constexpr (E::NEN == 4) h.cn[3] = w.y >> 16;
     } else {
-        T c[3][3];
-        c[0][0] = H[1][1] * H[2][2] - H[1][2] * H[2][1];
-        c[0][1] = H[1][2] * H[2][0] - H[1][0] * H[2][2];
-        c[0][2] = H[1][0] * H[2][1] - H[1][1] * H[2][0];
-        c[1][0] = H[0][2] * H[2][1] - H[0][1] * H[2][2];
-        c[1][1] = H[0][0] * H[2][2] - H[0][2] * H[2][0];
-        c[1][2] = H[0][1] * H[2][0] - H[0][0] * H[2][1];
-        c[2][0] = H[0][1] * H[1][2] - H[0][2] * H[1][1];
-        c[2][1] = H[0][2] * H[1][0] - H[0][0] * H[1][2];
-        c[2][2] = H[0][0] * H[1][1] - H[0][1] * H[1][0];
-        T I2 = c[0][0] + c[1][1] + c[2][2];
-        T detH = H[0][0] * c[0][0] + H[0][1] * c[0][1] + H[0][2] * c[0][2];
-        T s = I2 + detH;
-        T Jm1 = k.trH + s;
-        T J = T(1) + Jm1;
-        k.ok = J > T(0);
-        T rJ = rcp_(J);
-        // cof(F) - J I = cof(H) - H^T - (I2 + det H) I
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) k.G[i][j] = (c[i][j] - H[j][i] - (i == j ? s : T(0))) * rJ;
-        k.lnJ = k.ok ? log1p_(Jm1) : T(0);
+        uint4 w = reinterpret_cast<const uint4*>(rec)[lane];
+        h.cn[0] = w.x & 0xffff;
+        h.cn[1] = w.x >> 16;
+        h.cn[2] = w.y & 0xffff;
+        h.cn[3] = w.y >> 16;
+        h.cn[4] = w.z & 0xffff;
+        h.cn[5] = w.z >> 16;
+        h.cn[6] = w.w & 0xffff;
+        h.cn[7] = w.w >> 16;
     }
-}
-
-// psi = mu (tr H + H:H/2 - ln J) + lam/2 ln^2 J  (= mu/2 (I1-3) - mu lnJ + lam/2 ln^2 J)
-// scale = mu (I1/2 + |ln J|) + lam/2 ln^2 J, I1 = 3 + 2 tr H + H:H
-template <int D, typename T>
-__device__ __forceinline__ void density(const Kin<D, T>& k, T mu, T lam, T& psi, T& scale) {
-    T l2 = T(0.5) * lam * k.lnJ * k.lnJ;
-    psi = mu * (k.trH + T(0.5) * k.HH - k.lnJ) + l2;
-    T I1 = T(3) + T(2) * k.trH + k.HH;
-    scale = mu * (T(0.5) * I1 + fabs(k.lnJ)) + l2;
-}
-
-// P = mu (F - F^-T) + lam ln J F^-T = mu (H - G) + lam lnJ (I + G)
-template <int D, typename T>
-__device__ __forceinline__ void stress(const T (&H)[D][D], const Kin<D, T>& k, T mu, T lam,
-                                       T (&P)[D][D]) {
-    T ll = lam * k.lnJ;
+    const T* el = reinterpret_cast<const T*>(rec + p.conn_bytes) + lane * p.stride;
+    if (p.has_mat) {
+        lds_elem<T, E::NG + 2>(el, p.stride, h.ed);
+    } else {
+        if constexpr (E::NG > 0) {
+            T g[E::NG];
+            lds_elem<T, E::NG>(el, p.stride, g);
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j)
-            P[i][j] = mu * (H[i][j] - k.G[i][j]) + ll * (k.G[i][j] + (i == j ? T(1) : T(0)));
-}
-
-// dP = mu dF + (mu - lam lnJ) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
-template <int D, typename T>
-__device__ __forceinline__ void tangent(const T (&dF)[D][D], const Kin<D, T>& k, T mu, T lam,
-                                        T (&dP)[D][D]) {
-    T FiT[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) FiT[i][j] = k.G[i][j] + (i == j ? T(1) : T(0));
-    T trA = 0;  // tr(F^-1 dF) = F^-T : dF
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) trA = fma(FiT[i][j], dF[i][j], trA);
-    T M[D][D];  // dF^T F^-T
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T s = 0;
-#pragma unroll
-            for (int l = 0; l < D; ++l) s = fma(dF[l][a], FiT[l][j], s);
-            M[a][j] = s;
+            for (int j = 0; j < E::NG; ++j) h.ed[j] = g[j];
         }
-    T c1 = mu - lam * k.lnJ;
-    T c2 = lam * trA;
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T B = 0;  // (F^-T M)_ij
-#pragma unroll
-            for (int a = 0; a < D; ++a) B = fma(FiT[i][a], M[a][j], B);
-            dP[i][j] = mu * dF[i][j] + c1 * B + c2 * FiT[i][j];
-        }
+        h.ed[E::NG] = (T)p.mu0;
+        h.ed[E::NG + 1] = (T)p.lam0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -311,136 +343,449 @@ __host__ __device__ constexpr int hex_sign(int a, int j) {
                   : (j == 1 ? (((a & 3) >= 2) ? 1 : -1) : ((a >= 4) ? 1 : -1));
 }
 
-__host__ __device__ constexpr double hex_xi(int q, int j) {
-    return ((q >> j) & 1) ? kGauss : -kGauss;
-}
+__host__ __device__ constexpr double hex_xi(int q, int j) { return ((q >> j) & 1) ? kGauss : -kGauss; }
 
 // d N_a / d xi_j at Gauss point q
 __host__ __device__ constexpr double hex_dN(int a, int q, int j) {
-    double f0 = 1.0 + hex_sign(a, 0) * hex_xi(q, 0);
-    double f1 = 1.0 + hex_sign(a, 1) * hex_xi(q, 1);
-    double f2 = 1.0 + hex_sign(a, 2) * hex_xi(q, 2);
-    return j == 0 ? 0.125 * hex_sign(a, 0) * f1 * f2
-                  : (j == 1 ? 0.125 * hex_sign(a, 1) * f0 * f2 : 0.125 * hex_sign(a, 2) * f0 * f1);
+    return j == 0 ? 0.125 * hex_sign(a, 0) * (1.0 + hex_sign(a, 1) * hex_xi(q, 1)) *
+                        (1.0 + hex_sign(a, 2) * hex_xi(q, 2))
+           : j == 1 ? 0.125 * hex_sign(a, 1) * (1.0 + hex_sign(a, 0) * hex_xi(q, 0)) *
+                          (1.0 + hex_sign(a, 2) * hex_xi(q, 2))
+                    : 0.125 * hex_sign(a, 2) * (1.0 + hex_sign(a, 0) * hex_xi(q, 0)) *
+                          (1.0 + hex_sign(a, 1) * hex_xi(q, 1));
 }
 
 // ---------------------------------------------------------------------------
-// per-element work.  `ue`, `ve`, `xe` hold the gathered nodal vectors; results
-// go to f[NEN][AW] (nodal contributions) and the scalar accumulators.
+// quadrature-point work, shared by P1 and Q1
 // ---------------------------------------------------------------------------
-template <int D, typename T>
-__device__ __forceinline__ void outer_sum(const T (*du)[D], const T (*g)[D], int n, T (&H)[D][D]) {
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) H[i][j] = 0;
-    for (int a = 0; a < n; ++a)
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) H[i][j] = fma(du[a][i], g[a][j], H[i][j]);
-}
-
 struct ScalarAcc {
     double s0 = 0, s1 = 0;
     int ninv = 0;
 };
 
-// Quadrature-point work common to P1 and Q1: given H (and dF), the gradients
-// g[a] of the NEN-1 non-reference nodes and wdJ, produce the contributions
-// f[a] for those nodes (the reference node gets minus their sum).
-template <int OP, int D, int NM1, typename T>
-__device__ __forceinline__ void qp_work(const T (&H)[D][D], const T (&dF)[D][D], const T (&g)[NM1][D],
-                                        T wdJ, T mu, T lam, T (&f)[NM1 + 1][6], ScalarAcc& acc,
-                                        const T (&da)[D][D], double& gmu, double& glam, bool& inv) {
-    Kin<D, T> k;
-    kinematics<D, T>(H, k);
-    if (!k.ok) {
-        inv = true;
-        acc.ninv++;
-        return;
+template <int D, class V>
+__device__ __forceinline__ void outer_sum(const V (*du)[D], const V (*g)[D], int n, V (&H)[D][D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            V s = du[0][i] * g[0][j];
+            for (int a = 1; a < n; ++a) s = vfma(du[a][i], g[a][j], s);
+            H[i][j] = s;
+        }
+}
+
+// Given H (and dF), the gradients g of the NM1 non-reference nodes, w detJ
+// and the moduli, accumulate contributions f[a] for those nodes (f[NM1] is the
+// reference node for the block diagonal) and the scalar sums.  `valid` has a
+// bit per lane-vector component that holds a real element.
+template <int OP, int D, int NM1, class V>
+__device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D], const V (&g)[NM1][D],
+                                        V wdJ, V mu, V lam, int valid, V (&f)[NM1 + 1][6],
+                                        ScalarAcc& acc, double (&gmu)[2], double (&glam)[2],
+                                        int& inv) {
+    using S = typename VT<V>::S;
+    constexpr int N = VT<V>::N;
+    Kin<D, V> k;
+    kinematics<D, V>(H, k);
+    const int bad = valid & ~k.ok;
+    if (bad) {
+        inv |= bad;
+        acc.ninv += __popc(bad);
     }
+    const int good = valid & k.ok;
+    wdJ = vsel(good, wdJ, S(0));  // inverted or empty halves contribute nothing
     if constexpr (OP == OP_ENERGY) {
-        T psi, sc;
-        density<D, T>(k, mu, lam, psi, sc);
-        acc.s0 += (double)(wdJ * psi);
-        acc.s1 += (double)(wdJ * sc);
+        V psi, sc;
+        density<D, V>(k, mu, lam, psi, sc);
+        const V a = wdJ * psi, b = wdJ * sc;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            acc.s0 += vget(a, c);
+            acc.s1 += vget(b, c);
+        }
     } else if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
-        T P[D][D];
+        V P[D][D];
         if constexpr (OP == OP_RESIDUAL) {
-            stress<D, T>(H, k, mu, lam, P);
+            stress<D, V>(H, k, mu, lam, P);
         } else {
-            tangent<D, T>(dF, k, mu, lam, P);
-            T s = 0;
+            tangent<D, V>(dF, k, mu, lam, P);
+            V s = P[0][0] * dF[0][0];
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
-                for (int j = 0; j < D; ++j) s = fma(P[i][j], dF[i][j], s);
-            acc.s0 += (double)(wdJ * s);
+                for (int j = 0; j < D; ++j)
+                    if (i + j > 0) s = vfma(P[i][j], dF[i][j], s);
+            const V e = wdJ * s;
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc.s0 += vget(e, c);
         }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) P[i][j] = P[i][j] * wdJ;
 #pragma unroll
         for (int a = 0; a < NM1; ++a)
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                T s = 0;
+                V s = f[a][i];
 #pragma unroll
-                for (int j = 0; j < D; ++j) s = fma(P[i][j], g[a][j], s);
-                f[a][i] = fma(wdJ, s, f[a][i]);
+                for (int j = 0; j < D; ++j) s = vfma(P[i][j], g[a][j], s);
+                f[a][i] = s;
             }
     } else if constexpr (OP == OP_BLOCKDIAG) {
         // K_aa = wdJ [mu |g0|^2 I + (mu - lam lnJ + lam) gp gp^T], gp = F^-T g0
-        T c = wdJ * (mu + lam * (T(1) - k.lnJ));
-        T m = wdJ * mu;
+        const V c = wdJ * vfma(lam, splat<V>(S(1)) - k.lnJ, mu);
+        const V m = wdJ * mu;
 #pragma unroll
         for (int a = 0; a <= NM1; ++a) {
-            T g0[D];
+            V g0[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 if (a < NM1) {
                     g0[j] = g[a][j];
                 } else {
-                    T s = 0;
+                    V s = -g[0][j];
 #pragma unroll
-                    for (int b = 0; b < NM1; ++b) s -= g[b][j];
+                    for (int b = 1; b < NM1; ++b) s = s - g[b][j];
                     g0[j] = s;
                 }
             }
-            T gp[D];
-            T n2 = 0;
+            V gp[D];
+            V n2 = g0[0] * g0[0];
+#pragma unroll
+            for (int i = 1; i < D; ++i) n2 = vfma(g0[i], g0[i], n2);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                T s = g0[i];
+                V s = g0[i];
 #pragma unroll
-                for (int j = 0; j < D; ++j) s = fma(k.G[i][j], g0[j], s);
+                for (int j = 0; j < D; ++j) s = vfma(k.G[i][j], g0[j], s);
                 gp[i] = s;
-                n2 = fma(g0[i], g0[i], n2);
             }
-            T mn = m * n2;
+            const V mn = m * n2;
             if constexpr (D == 3) {
-                f[a][0] += mn + c * gp[0] * gp[0];
-                f[a][1] += mn + c * gp[1] * gp[1];
-                f[a][2] += mn + c * gp[2] * gp[2];
-                f[a][3] += c * gp[0] * gp[1];
-                f[a][4] += c * gp[0] * gp[2];
-                f[a][5] += c * gp[1] * gp[2];
+                f[a][0] = f[a][0] + vfma(c * gp[0], gp[0], mn);
+                f[a][1] = f[a][1] + vfma(c * gp[1], gp[1], mn);
+                f[a][2] = f[a][2] + vfma(c * gp[2], gp[2], mn);
+                f[a][3] = vfma(c * gp[0], gp[1], f[a][3]);
+                f[a][4] = vfma(c * gp[0], gp[2], f[a][4]);
+                f[a][5] = vfma(c * gp[1], gp[2], f[a][5]);
             } else {
-                f[a][0] += mn + c * gp[0] * gp[0];
-                f[a][1] += mn + c * gp[1] * gp[1];
-                f[a][2] += c * gp[0] * gp[1];
+                f[a][0] = f[a][0] + vfma(c * gp[0], gp[0], mn);
+                f[a][1] = f[a][1] + vfma(c * gp[1], gp[1], mn);
+                f[a][2] = vfma(c * gp[0], gp[1], f[a][2]);
             }
         }
     } else if constexpr (OP == OP_PVJP) {
         // dP/dmu : grad a = (H - G) : grad a ; dP/dlam : grad a = lnJ (I + G) : grad a
-        T sm = 0, sl = 0;
+        V sm = splat<V>(S(0)), sl = splat<V>(S(0));
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                sm = fma(H[i][j] - k.G[i][j], da[i][j], sm);
-                sl = fma(k.G[i][j] + (i == j ? T(1) : T(0)), da[i][j], sl);
+                sm = vfma(H[i][j] - k.G[i][j], dF[i][j], sm);
+                sl = vfma(k.G[i][j], dF[i][j], sl);
+                if (i == j) sl = sl + dF[i][j];
             }
-        gmu += (double)(wdJ * sm);
-        glam += (double)(wdJ * k.lnJ * sl);
+        const V a = wdJ * sm, b = wdJ * k.lnJ * sl;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            gmu[c] += vget(a, c);
+            glam[c] += vget(b, c);
+        }
+    }
+}
+
+template <int N, int ET, typename T>
+struct Packer;
+template <int ET, typename T>
+struct Packer<1, ET, T> {
+    __device__ __forceinline__ static T ed(const Half<ET, T>* hs, int j) { return hs[0].ed[j]; }
+};
+template <int ET, typename T>
+struct Packer<2, ET, T> {
+    __device__ __forceinline__ static F2 ed(const Half<ET, T>* hs, int j) {
+        return mk2((float)hs[0].ed[j], (float)hs[1].ed[j]);
+    }
+};
+
+// element of a round pair / single: gather, compute, return contributions
+template <int ET, typename T, int OP, class V>
+__device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, const T* sU, const T* sV,
+                                             const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc& acc,
+                                             double (&gmu)[2], double (&glam)[2], int& inv) {
+    using E = ElemT<ET>;
+    using S = typename VT<V>::S;
+    constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1, NG = E::NG;
+    constexpr int N = VT<V>::N;
+    using PK = Packer<N, ET, T>;
+    constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
+    V ue[NEN][D], ve[NEN][D];
+#pragma unroll
+    for (int a = 0; a < NEN; ++a) {
+        T t0[4], t1[4];
+        lds_vec<VW, T>(sU, hs[0].cn[a], t0);
+        if constexpr (N == 2) lds_vec<VW, T>(sU, hs[N - 1].cn[a], t1);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            if constexpr (N == 2)
+                ue[a][c] = mk2(t0[c], t1[c]);
+            else
+                ue[a][c] = (V)t0[c];
+        }
+        if constexpr (kNeedV) {
+            lds_vec<VW, T>(sV, hs[0].cn[a], t0);
+            if constexpr (N == 2) lds_vec<VW, T>(sV, hs[N - 1].cn[a], t1);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                if constexpr (N == 2)
+                    ve[a][c] = mk2(t0[c], t1[c]);
+                else
+                    ve[a][c] = (V)t0[c];
+            }
+        }
+    }
+    const V mu = PK::ed(hs, NG);
+    const V lam = PK::ed(hs, NG + 1);
+#pragma unroll
+    for (int a = 0; a < NEN; ++a)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[a][c] = splat<V>(S(0));
+
+    if constexpr (ET != 2) {
+        // P1: reference node = last; grad N_a (a < NEN-1) and w detJ from the record
+        V g[NM1][D];
+#pragma unroll
+        for (int a = 0; a < NM1; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) g[a][c] = PK::ed(hs, a * D + c);
+        const V wdJ = PK::ed(hs, NG - 1);
+        V du[NM1][D], dv[NM1][D];
+#pragma unroll
+        for (int a = 0; a < NM1; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                du[a][c] = ue[a][c] - ue[NM1][c];
+                if constexpr (kNeedV) dv[a][c] = ve[a][c] - ve[NM1][c];
+            }
+        V H[D][D], dF[D][D];
+        outer_sum<D, V>(du, g, NM1, H);
+        if constexpr (kNeedV) {
+            outer_sum<D, V>(dv, g, NM1, dF);
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) dF[i][j] = splat<V>(S(0));
+        }
+        V fq[NM1 + 1][6];
+#pragma unroll
+        for (int a = 0; a <= NM1; ++a)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fq[a][c] = splat<V>(S(0));
+        qp_work<OP, D, NM1, V>(H, dF, g, wdJ, mu, lam, valid, fq, acc, gmu, glam, inv);
+        if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                V s = -fq[0][c];
+                f[0][c] = fq[0][c];
+#pragma unroll
+                for (int a = 1; a < NM1; ++a) {
+                    f[a][c] = fq[a][c];
+                    s = s - fq[a][c];
+                }
+                f[NM1][c] = s;
+            }
+        } else if constexpr (OP == OP_BLOCKDIAG) {
+#pragma unroll
+            for (int a = 0; a <= NM1; ++a)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) f[a][c] = fq[a][c];
+        }
+    } else {
+        // Q1: reference node 0; J rebuilt at each Gauss point
+        V dx[NM1][D], du[NM1][D], dv[NM1][D];
+        {
+            T x0[4];
+            lds_vec<VW, T>(sX, hs[0].cn[0], x0);
+#pragma unroll
+            for (int a = 1; a < NEN; ++a) {
+                T t[4];
+                lds_vec<VW, T>(sX, hs[0].cn[a], t);
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    dx[a - 1][c] = (V)(t[c] - x0[c]);
+                    du[a - 1][c] = ue[a][c] - ue[0][c];
+                    if constexpr (kNeedV) dv[a - 1][c] = ve[a][c] - ve[0][c];
+                }
+            }
+        }
+        V fr[NEN][6];  // nodes 1..7, then node 0 (block diagonal)
+#pragma unroll
+        for (int a = 0; a < NEN; ++a)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fr[a][c] = splat<V>(S(0));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            V gr[NM1][D];
+#pragma unroll
+            for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                for (int j = 0; j < D; ++j) gr[a][j] = (V)hex_dN(a + 1, q, j);
+            V Jm[D][D];
+            outer_sum<D, V>(dx, gr, NM1, Jm);
+            const V c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+            const V c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+            const V c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+            const V detJ = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
+            const V rd = vrcp(detJ);
+            V Ji[3][3];
+            Ji[0][0] = c00 * rd;
+            Ji[1][0] = c01 * rd;
+            Ji[2][0] = c02 * rd;
+            Ji[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) * rd;
+            Ji[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) * rd;
+            Ji[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) * rd;
+            Ji[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) * rd;
+            Ji[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) * rd;
+            Ji[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) * rd;
+            V g[NM1][D];
+#pragma unroll
+            for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    V s = Ji[0][i] * gr[a][0];
+#pragma unroll
+                    for (int j = 1; j < D; ++j) s = vfma(Ji[j][i], gr[a][j], s);
+                    g[a][i] = s;
+                }
+            V H[D][D], dF[D][D];
+            outer_sum<D, V>(du, g, NM1, H);
+            if constexpr (kNeedV) {
+                outer_sum<D, V>(dv, g, NM1, dF);
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) dF[i][j] = splat<V>(S(0));
+            }
+            qp_work<OP, D, NM1, V>(H, dF, g, detJ, mu, lam, valid, fr, acc, gmu, glam, inv);
+        }
+        if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                V s = -fr[0][c];
+                f[1][c] = fr[0][c];
+#pragma unroll
+                for (int a = 1; a < NM1; ++a) {
+                    f[a + 1][c] = fr[a][c];
+                    s = s - fr[a][c];
+                }
+                f[0][c] = s;
+            }
+        } else if constexpr (OP == OP_BLOCKDIAG) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                f[0][c] = fr[NM1][c];
+#pragma unroll
+                for (int a = 0; a < NM1; ++a) f[a + 1][c] = fr[a][c];
+            }
+        }
+    }
+}
+
+// block-diagonal entries (packed symmetric) -> full D x D with the Dirichlet identity
+template <int D, typename T>
+__device__ __forceinline__ int write_block(T* out, int64_t g, const T* s, uint8_t m) {
+    T Dm[D][D];
+    if constexpr (D == 3) {
+        Dm[0][0] = s[0];
+        Dm[1][1] = s[1];
+        Dm[2][2] = s[2];
+        Dm[0][1] = Dm[1][0] = s[3];
+        Dm[0][2] = Dm[2][0] = s[4];
+        Dm[1][2] = Dm[2][1] = s[5];
+    } else {
+        Dm[0][0] = s[0];
+        Dm[1][1] = s[1];
+        Dm[0][1] = Dm[1][0] = s[2];
+    }
+    int fl = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            T x = Dm[a][b];
+            if (((m >> a) & 1) || ((m >> b) & 1)) x = (a == b) ? T(1) : T(0);
+            if (!finite_(x)) fl |= 2;
+            out[(g * D + a) * D + b] = x;
+        }
+    return fl;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ int write_vec(T* out, int64_t g, const T* s, uint8_t m, unsigned flags) {
+    int fl = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T x = s[c];
+        if ((flags & 1u) && ((m >> c) & 1)) x = T(0);
+        if (!finite_(x)) fl |= 2;
+        out[g * D + c] = x;
+    }
+    return fl;
+}
+
+// Neumaier step: (s, c) += x
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+// Fixed-order FP64 reduction of the tile partials tile_red[t][0..2] by one
+// block of nthreads threads: strided per-thread Neumaier sums, a warp
+// butterfly on (sum, compensation), then the warps in order.  `scratch` holds
+// 4 doubles per warp.  Returns the totals in thread 0.
+__device__ __forceinline__ void reduce_tiles(const double* tile_red, int n_tiles, int nthreads,
+                                             double* scratch, double& S0, double& S1, double& N) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double sum0 = 0, c0 = 0, sum1 = 0, c1 = 0, cnt = 0;
+    for (int t = tid; t < n_tiles; t += nthreads) {
+        neumaier(sum0, c0, __ldcg(tile_red + (int64_t)t * 4 + 0));
+        neumaier(sum1, c1, __ldcg(tile_red + (int64_t)t * 4 + 1));
+        cnt += __ldcg(tile_red + (int64_t)t * 4 + 2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, sum0, o);
+        const double oc = __shfl_xor_sync(0xffffffffu, c0, o);
+        const double ps = __shfl_xor_sync(0xffffffffu, sum1, o);
+        const double pc = __shfl_xor_sync(0xffffffffu, c1, o);
+        const double on = __shfl_xor_sync(0xffffffffu, cnt, o);
+        c0 += oc;
+        neumaier(sum0, c0, os);
+        c1 += pc;
+        neumaier(sum1, c1, ps);
+        cnt += on;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        scratch[warp * 4 + 0] = sum0 + c0;
+        scratch[warp * 4 + 1] = sum1 + c1;
+        scratch[warp * 4 + 2] = cnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a0 = 0, k0 = 0, a1 = 0, k1 = 0, n = 0;
+        for (int w = 0; w < nthreads / 32; ++w) {
+            neumaier(a0, k0, scratch[w * 4 + 0]);
+            neumaier(a1, k1, scratch[w * 4 + 1]);
+            n += scratch[w * 4 + 2];
+        }
+        S0 = a0 + k0;
+        S1 = a1 + k1;
+        N = n;
     }
 }
 
@@ -450,63 +795,104 @@ __device__ __forceinline__ void qp_work(const T (&H)[D][D], const T (&dF)[D][D],
 template <int ET, typename T, int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     using E = ElemT<ET>;
-    constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1;
+    constexpr int D = E::D, NEN = E::NEN, VW = E::VW;
+    constexpr int NR = rounds_per_iter(ET, (int)sizeof(T));
+    using V = typename std::conditional<NR == 2, F2, T>::type;
     constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
 
     const int tile = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n0 = p.tile_node_ptr[tile];
     const int nl = (int)(p.tile_node_ptr[tile + 1] - n0);
-    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, nl);
+    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, nl, p.rec_bytes);
     const int AW = L.aw;
     T* sU = reinterpret_cast<T*>(smem + L.off_u);
     T* sV = reinterpret_cast<T*>(smem + L.off_v);
     T* sX = reinterpret_cast<T*>(smem + L.off_x);
     T* sAcc = reinterpret_cast<T*>(smem + L.off_acc);
+    int32_t* sGid = reinterpret_cast<int32_t*>(smem + L.off_gid);
+    int32_t* sSlot = reinterpret_cast<int32_t*>(smem + L.off_slot);
     uint8_t* sMask = smem + L.off_mask;
     double* sRed = reinterpret_cast<double*>(smem + L.off_red);
     int* sFlag = reinterpret_cast<int*>(smem + L.off_red + kWarps * 4 * 8);
+    uint8_t* ring = smem + L.off_ring + warp * kStages * L.stage_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp * kStages;
 
     const T* gu = static_cast<const T*>(p.u);
     const T* gv = static_cast<const T*>(p.v);
     int flags_local = 0;
 
-    // 1. stage the tile's nodes
-    for (int i = tid; i < nl; i += kThreads) {
-        const int g = p.node_gid[n0 + i];
-        const uint8_t m = p.node_mask[g];
-        T t[4] = {0, 0, 0, 0};
-        bool fin = true;
+    // 0. this warp's contiguous range of the tile's rounds; start its copies
+    const int r_begin = p.tile_round_ptr[tile], R = p.tile_round_ptr[tile + 1] - r_begin;
+    const int my_r0 = r_begin + warp * (R / kWarps) + min(warp, R % kWarps);
+    const int my_n = R / kWarps + (warp < R % kWarps ? 1 : 0);
+    const int n_it = (my_n + NR - 1) / NR;
+    if (lane == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    auto issue = [&](int it) {
+        const int r = my_r0 + it * NR;
+        const int nrec = min(NR, my_n - it * NR);
+        bulk_load(ring + (it % kStages) * L.stage_bytes, p.rec + (int64_t)r * p.rec_bytes,
+                  (uint32_t)(nrec * p.rec_bytes), &bars[it % kStages]);
+    };
+    if (lane == 0)
+        for (int it = 0; it < n_it && it < kStages; ++it) issue(it);
+    // valid-lane counts of this warp's rounds, one per lane (at most 32 rounds)
+    const int my_nv = (lane < my_n) ? p.round_nvalid[my_r0 + lane] : 0;
+
+    // 1. stage the tile's nodes; zero the accumulators
+    for (int base = 0; base < nl; base += 4 * kThreads) {
+        int gid[4], slot[4];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            t[k] = gu[(int64_t)g * D + k];
-            fin = fin && finite_(t[k]);
+        for (int j = 0; j < 4; ++j) {
+            const int i = base + j * kThreads + tid;
+            gid[j] = (i < nl) ? p.node_gid[n0 + i] : 0;
+            slot[j] = (i < nl) ? p.node_slot[n0 + i] : 0;
         }
-        sts_vec<VW, T>(sU, i, t);
-        if constexpr (kNeedV) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                T x = gv[(int64_t)g * D + k];
-                if (OP == OP_HVP && (p.flags & 2u) && ((m >> k) & 1)) x = T(0);
-                fin = fin && finite_(x);
-                t[k] = x;
+        for (int j = 0; j < 4; ++j) {
+            const int i = base + j * kThreads + tid;
+            if (i >= nl) continue;
+            const int64_t g = gid[j];
+            const uint8_t m = p.node_mask[g];
+            T t[4] = {0, 0, 0, 0};
+            bool fin = true;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                t[c] = gu[g * D + c];
+                fin = fin && finite_(t[c]);
             }
-            sts_vec<VW, T>(sV, i, t);
-        }
-        if constexpr (ET == 2) {
-            const T* gx = static_cast<const T*>(p.X);
+            sts_vec<VW, T>(sU, i, t);
+            if constexpr (kNeedV) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) t[k] = gx[(int64_t)g * D + k];
-            sts_vec<VW, T>(sX, i, t);
+                for (int c = 0; c < D; ++c) {
+                    T x = gv[g * D + c];
+                    if (OP == OP_HVP && (p.flags & 2u) && ((m >> c) & 1)) x = T(0);
+                    fin = fin && finite_(x);
+                    t[c] = x;
+                }
+                sts_vec<VW, T>(sV, i, t);
+            }
+            if constexpr (ET == 2) {
+                const T* gx = static_cast<const T*>(p.X);
+#pragma unroll
+                for (int c = 0; c < D; ++c) t[c] = gx[g * D + c];
+                sts_vec<VW, T>(sX, i, t);
+            }
+            if (!fin) flags_local |= 2;
+            sMask[i] = m;
+            sGid[i] = gid[j];
+            sSlot[i] = slot[j];
         }
-        if (!fin) flags_local |= 2;
-        sMask[i] = m;
-        if constexpr (kNeedAcc) {
-            for (int w = 0; w < kWarps; ++w)
-                for (int k = 0; k < AW; ++k) sAcc[((int64_t)w * nl + i) * AW + k] = T(0);
-        }
+    }
+    if constexpr (kNeedAcc) {
+        int4* z = reinterpret_cast<int4*>(sAcc);
+        for (int j = tid; j < L.acc_bytes / 16; j += kThreads) z[j] = make_int4(0, 0, 0, 0);
     }
     if (tid == 0) *sFlag = 0;
     __syncthreads();
@@ -514,207 +900,81 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     // 2. rounds
     ScalarAcc acc;
     T* myAcc = sAcc + (int64_t)warp * nl * AW;
-    const int r_begin = p.tile_round_ptr[tile], r_end = p.tile_round_ptr[tile + 1];
-    bool inv = false;
-    for (int r = r_begin + warp; r < r_end; r += kWarps) {
-        const int nv = p.round_nvalid[r];
-        const uint8_t* rec = p.rec + (int64_t)r * p.rec_bytes;
-        if (lane < nv) {
-            int cn[NEN];
-            if constexpr (E::PAD == 4) {
-                uint2 w = __ldg(reinterpret_cast<const uint2*>(rec) + lane);
-                cn[0] = w.x & 0xffff;
-                cn[1] = w.x >> 16;
-                cn[2] = w.y & 0xffff;
-                if constexpr (NEN == 4) cn[3] = w.y >> 16;
-            } else {
-                uint4 w = __ldg(reinterpret_cast<const uint4*>(rec) + lane);
-                cn[0] = w.x & 0xffff;
-                cn[1] = w.x >> 16;
-                cn[2] = w.y & 0xffff;
-                cn[3] = w.y >> 16;
-                cn[4] = w.z & 0xffff;
-                cn[5] = w.z >> 16;
-                cn[6] = w.w & 0xffff;
-                cn[7] = w.w >> 16;
-            }
-            T mu = (T)p.mu0, lam = (T)p.lam0;
-            if (p.mat_off >= 0) {
-                const T* mat = reinterpret_cast<const T*>(rec + p.mat_off);
-                mu = ldg_(mat + lane);
-                lam = ldg_(mat + 32 + lane);
-            }
-            // gather
-            T ue[NEN][D], ve[NEN][D];
+    int inv = 0;
+    bool timed_out = false;
+    int it = 0;
+    for (; it < n_it; ++it) {
+        const int s = it % kStages;
+        if (!mbar_wait_bounded(&bars[s], (uint32_t)((it / kStages) & 1))) {
+            timed_out = true;
+            break;
+        }
+        const int k0 = it * NR;
+        const uint8_t* st = ring + s * L.stage_bytes;
+        Half<ET, T> hs[NR];
+        int valid = 0;
+#pragma unroll
+        for (int h = 0; h < NR; ++h) {
+            const int nv = __shfl_sync(0xffffffffu, my_nv, (k0 + h) & 31);
+            const bool ok = (k0 + h < my_n) && lane < nv;
+            valid |= ok ? (1 << h) : 0;
+            read_half<ET, T>(st + h * p.rec_bytes, lane, ok, p, hs[h]);
+        }
+        __syncwarp();
+        if (lane == 0 && it + kStages < n_it) {
+            fence_proxy_async_smem();
+            issue(it + kStages);
+        }
+        V f[NEN][6];
+        // add half h of the lane's contributions into the warp's accumulator
+        auto scatter = [&](int h) {
 #pragma unroll
             for (int a = 0; a < NEN; ++a) {
-                T t[4];
-                lds_vec<VW, T>(sU, cn[a], t);
+                const int n = hs[h].cn[a];
+                if constexpr (OP == OP_BLOCKDIAG) {
 #pragma unroll
-                for (int k = 0; k < D; ++k) ue[a][k] = t[k];
-                if constexpr (kNeedV) {
-                    lds_vec<VW, T>(sV, cn[a], t);
+                    for (int c = 0; c < (D == 3 ? 6 : 3); ++c) myAcc[n * AW + c] += vcomp(f[a][c], h);
+                } else {
+                    T cur[4];
+                    lds_vec<VW, T>(myAcc, n, cur);
 #pragma unroll
-                    for (int k = 0; k < D; ++k) ve[a][k] = t[k];
+                    for (int c = 0; c < D; ++c) cur[c] += vcomp(f[a][c], h);
+                    sts_vec<VW, T>(myAcc, n, cur);
                 }
             }
-            T f[NEN][6];
-#pragma unroll
-            for (int a = 0; a < NEN; ++a)
-#pragma unroll
-                for (int k = 0; k < 6; ++k) f[a][k] = 0;
-            double gmu = 0, glam = 0;
-
-            if constexpr (ET != 2) {
-                // P1: reference node = last; grad N_a (a < NEN-1) and w detJ precomputed
-                const T* geom = reinterpret_cast<const T*>(rec + p.geom_off);
-                T g[NM1][D];
-#pragma unroll
-                for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                    for (int k = 0; k < D; ++k) g[a][k] = ldg_(geom + (a * D + k) * 32 + lane);
-                const T wdJ = ldg_(geom + (E::NG - 1) * 32 + lane);
-                T du[NM1][D], dv[NM1][D];
-#pragma unroll
-                for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        du[a][k] = ue[a][k] - ue[NM1][k];
-                        if constexpr (kNeedV) dv[a][k] = ve[a][k] - ve[NM1][k];
-                    }
-                T H[D][D], dF[D][D] = {};
-                outer_sum<D, T>(du, g, NM1, H);
-                if constexpr (kNeedV) outer_sum<D, T>(dv, g, NM1, dF);
-                T fq[NM1 + 1][6];
-#pragma unroll
-                for (int a = 0; a <= NM1; ++a)
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) fq[a][k] = 0;
-                qp_work<OP, D, NM1, T>(H, dF, g, wdJ, mu, lam, fq, acc, dF, gmu, glam, inv);
-                if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        T s = 0;
-#pragma unroll
-                        for (int a = 0; a < NM1; ++a) {
-                            f[a][k] = fq[a][k];
-                            s -= fq[a][k];
-                        }
-                        f[NM1][k] = s;
-                    }
-                } else if constexpr (OP == OP_BLOCKDIAG) {
-#pragma unroll
-                    for (int a = 0; a <= NM1; ++a)
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) f[a][k] = fq[a][k];
-                }
-            } else {
-                // Q1: reference node 0; J rebuilt at each Gauss point
-                T dx[NM1][D], du[NM1][D], dv[NM1][D];
-                {
-                    T x0[4];
-                    lds_vec<VW, T>(sX, cn[0], x0);
-#pragma unroll
-                    for (int a = 1; a < NEN; ++a) {
-                        T t[4];
-                        lds_vec<VW, T>(sX, cn[a], t);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            dx[a - 1][k] = t[k] - x0[k];
-                            du[a - 1][k] = ue[a][k] - ue[0][k];
-                            if constexpr (kNeedV) dv[a - 1][k] = ve[a][k] - ve[0][k];
-                        }
-                    }
-                }
-                T fr[NEN][6];  // contributions of nodes 1..7, then node 0 (block diagonal)
-#pragma unroll
-                for (int a = 0; a < NEN; ++a)
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) fr[a][k] = 0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    T gr[NM1][D];  // reference gradients of nodes 1..7
-#pragma unroll
-                    for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                        for (int j = 0; j < D; ++j) gr[a][j] = (T)hex_dN(a + 1, q, j);
-                    T Jm[D][D];
-                    outer_sum<D, T>(dx, gr, NM1, Jm);
-                    // inverse of J by cofactors
-                    T c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
-                    T c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
-                    T c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
-                    T detJ = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
-                    T rd = rcp_(detJ);
-                    T Ji[3][3];  // J^-1
-                    Ji[0][0] = c00 * rd;
-                    Ji[1][0] = c01 * rd;
-                    Ji[2][0] = c02 * rd;
-                    Ji[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) * rd;
-                    Ji[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) * rd;
-                    Ji[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) * rd;
-                    Ji[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) * rd;
-                    Ji[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) * rd;
-                    Ji[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) * rd;
-                    // physical gradients g_a = J^-T grad N^_a
-                    T g[NM1][D];
-#pragma unroll
-                    for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            T s = 0;
-#pragma unroll
-                            for (int j = 0; j < D; ++j) s = fma(Ji[j][i], gr[a][j], s);
-                            g[a][i] = s;
-                        }
-                    T H[D][D], dF[D][D] = {};
-                    outer_sum<D, T>(du, g, NM1, H);
-                    if constexpr (kNeedV) outer_sum<D, T>(dv, g, NM1, dF);
-                    qp_work<OP, D, NM1, T>(H, dF, g, detJ, mu, lam, fr, acc, dF, gmu, glam, inv);
-                }
-                if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        T s = 0;
-#pragma unroll
-                        for (int a = 0; a < NM1; ++a) {
-                            f[a + 1][k] = fr[a][k];
-                            s -= fr[a][k];
-                        }
-                        f[0][k] = s;
-                    }
-                } else if constexpr (OP == OP_BLOCKDIAG) {
-                    // qp_work put nodes 1..7 in rows 0..6 and node 0 in row 7
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        f[0][k] = fr[NM1][k];
-#pragma unroll
-                        for (int a = 0; a < NM1; ++a) f[a + 1][k] = fr[a][k];
-                    }
-                }
-            }
-
+        };
+        if (valid) {
+            double gmu[2] = {0, 0}, glam[2] = {0, 0};
+            element_work<ET, T, OP, V>(hs, valid, sU, sV, sX, f, acc, gmu, glam, inv);
             if constexpr (OP == OP_PVJP) {
-                const int e = p.round_elem[(int64_t)r * 32 + lane];
-                if (p.out_mu) p.out_mu[e] = gmu;
-                if (p.out_lam) p.out_lam[e] = glam;
-            }
-            if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll
-                for (int a = 0; a < NEN; ++a) rmw_vec<VW, D, T>(myAcc, cn[a], f[a]);
-            } else if constexpr (OP == OP_BLOCKDIAG) {
-#pragma unroll
-                for (int a = 0; a < NEN; ++a)
-                    for (int k = 0; k < AW; ++k) myAcc[cn[a] * AW + k] += f[a][k];
+                for (int h = 0; h < NR; ++h)
+                    if (valid & (1 << h)) {
+                        const int e = p.round_elem[(int64_t)(my_r0 + k0 + h) * 32 + lane];
+                        if (p.out_mu) p.out_mu[e] = gmu[h];
+                        if (p.out_lam) p.out_lam[e] = glam[h];
+                    }
             }
-            (void)gmu;
-            (void)glam;
+            if constexpr (kNeedAcc)
+                if (valid & 1) scatter(0);
         }
+        if constexpr (NR == 2 && kNeedAcc) {
+            __syncwarp();  // round k0 lands before round k0+1: they may share nodes
+            if (valid & 2) scatter(1);
+        }
+        __syncwarp();
+    }
+    if (timed_out) {
+        // drain the copies still in flight before the CTA may exit
+        flags_local |= 4;
+        if (lane == 0)
+            for (int j = it; j < n_it && j < it + kStages; ++j)
+                mbar_wait_bounded(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
         __syncwarp();
     }
     if (inv) flags_local |= 1;
 
-    // 3. block reductions of the scalar accumulators (fixed order)
+    // 3. block sums of the scalar accumulators (fixed order)
     if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
         double s0 = acc.s0, s1 = acc.s1, s2 = (double)acc.ninv;
 #pragma unroll
@@ -730,116 +990,48 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         }
     }
     {
-        int wf = __reduce_or_sync(0xffffffffu, flags_local);
+        const int wf = __reduce_or_sync(0xffffffffu, flags_local);
         if (lane == 0 && wf) atomicOr(sFlag, wf);
     }
     __syncthreads();
 
-    // 4. combine the warp copies and write nodal results
+    // 4. combine the warp copies; write private nodes and shared partials
     if constexpr (kNeedAcc) {
         T* part = static_cast<T*>(p.partial);
         T* out = static_cast<T*>(p.out);
         int wflag = 0;
         for (int i = tid; i < nl; i += kThreads) {
-            T s[6] = {0, 0, 0, 0, 0, 0};
-            for (int w = 0; w < kWarps; ++w)
-                for (int k = 0; k < AW; ++k) s[k] += sAcc[((int64_t)w * nl + i) * AW + k];
-            const int slot = p.node_slot[n0 + i];
-            const int g = p.node_gid[n0 + i];
-            if (slot < 0) {
-                const uint8_t m = sMask[i];
-                if constexpr (OP == OP_BLOCKDIAG) {
-                    T Dm[D][D];
-                    if constexpr (D == 3) {
-                        Dm[0][0] = s[0]; Dm[1][1] = s[1]; Dm[2][2] = s[2];
-                        Dm[0][1] = Dm[1][0] = s[3];
-                        Dm[0][2] = Dm[2][0] = s[4];
-                        Dm[1][2] = Dm[2][1] = s[5];
-                    } else {
-                        Dm[0][0] = s[0]; Dm[1][1] = s[1];
-                        Dm[0][1] = Dm[1][0] = s[2];
-                    }
-                    for (int a = 0; a < D; ++a)
-                        for (int b = 0; b < D; ++b) {
-                            T x = Dm[a][b];
-                            if (((m >> a) & 1) || ((m >> b) & 1)) x = (a == b) ? T(1) : T(0);
-                            if (!finite_(x)) wflag |= 2;
-                            out[((int64_t)g * D + a) * D + b] = x;
-                        }
-                } else {
-                    for (int k = 0; k < D; ++k) {
-                        T x = s[k];
-                        if ((p.flags & 1u) && ((m >> k) & 1)) x = T(0);
-                        if (!finite_(x)) wflag |= 2;
-                        out[(int64_t)g * D + k] = x;
-                    }
-                }
+            T sum[6] = {0, 0, 0, 0, 0, 0};
+            if constexpr (OP == OP_BLOCKDIAG) {
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w)
+                    for (int c = 0; c < AW; ++c) sum[c] += sAcc[((int64_t)w * nl + i) * AW + c];
             } else {
-                for (int k = 0; k < AW; ++k) part[(int64_t)slot * AW + k] = s[k];
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    T t[4];
+                    lds_vec<VW, T>(sAcc + (int64_t)w * nl * VW, i, t);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) sum[c] += t[c];
+                }
+            }
+            const int slot = sSlot[i];
+            if (slot < 0) {
+                if constexpr (OP == OP_BLOCKDIAG)
+                    wflag |= write_block<D, T>(out, sGid[i], sum, sMask[i]);
+                else
+                    wflag |= write_vec<D, T>(out, sGid[i], sum, sMask[i], p.flags);
+            } else if constexpr (OP == OP_BLOCKDIAG) {
+                for (int c = 0; c < AW; ++c) part[(int64_t)slot * AW + c] = sum[c];
+            } else {
+                sts_vec<VW, T>(part, slot, sum);  // one node vector per slot
             }
         }
         if (wflag) atomicOr(sFlag, wflag);
-        __threadfence();
-        __syncthreads();
-        // last arriver of each shared node sums its slots in slot order
-        for (int i = tid; i < nl; i += kThreads) {
-            const int slot = p.node_slot[n0 + i];
-            if (slot < 0) continue;
-            const int sid = p.slot_owner[slot];
-            const int64_t s0 = p.shared_slot_ptr[sid], s1 = p.shared_slot_ptr[sid + 1];
-            const int old = atomicAdd(&p.shared_count[sid], 1);
-            if (old != (int)(s1 - s0) - 1) continue;
-            __threadfence();
-            T s[6] = {0, 0, 0, 0, 0, 0};
-            for (int64_t q = s0; q < s1; ++q)
-                for (int k = 0; k < AW; ++k) s[k] += __ldcg(part + q * AW + k);
-            p.shared_count[sid] = 0;
-            const int g = p.node_gid[n0 + i];
-            const uint8_t m = sMask[i];
-            int fl = 0;
-            if constexpr (OP == OP_BLOCKDIAG) {
-                T Dm[D][D];
-                if constexpr (D == 3) {
-                    Dm[0][0] = s[0]; Dm[1][1] = s[1]; Dm[2][2] = s[2];
-                    Dm[0][1] = Dm[1][0] = s[3];
-                    Dm[0][2] = Dm[2][0] = s[4];
-                    Dm[1][2] = Dm[2][1] = s[5];
-                } else {
-                    Dm[0][0] = s[0]; Dm[1][1] = s[1];
-                    Dm[0][1] = Dm[1][0] = s[2];
-                }
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) {
-                        T x = Dm[a][b];
-                        if (((m >> a) & 1) || ((m >> b) & 1)) x = (a == b) ? T(1) : T(0);
-                        if (!finite_(x)) fl |= 2;
-                        out[((int64_t)g * D + a) * D + b] = x;
-                    }
-            } else {
-                for (int k = 0; k < D; ++k) {
-                    T x = s[k];
-                    if ((p.flags & 1u) && ((m >> k) & 1)) x = T(0);
-                    if (!finite_(x)) fl |= 2;
-                    out[(int64_t)g * D + k] = x;
-                }
-            }
-            if (fl) atomicOr(p.status, fl);
-        }
-        // nodes that belong to no element
-        if (tile == 0) {
-            for (int i = tid; i < p.n_orphans; i += kThreads) {
-                const int g = p.orphans[i];
-                if constexpr (OP == OP_BLOCKDIAG) {
-                    for (int a = 0; a < D; ++a)
-                        for (int b = 0; b < D; ++b) out[((int64_t)g * D + a) * D + b] = (a == b) ? T(1) : T(0);
-                } else {
-                    for (int k = 0; k < D; ++k) out[(int64_t)g * D + k] = T(0);
-                }
-            }
-        }
     }
 
-    // 5. tile partial of the scalars; the last tile reduces them in tile order
+    // 5. scalar tile partials; the energy's last tile reduces them in tile
+    //    order (the HVP's are reduced by finalize_kernel)
     if (OP == OP_ENERGY || (OP == OP_HVP && p.out_scalar != nullptr)) {
         __shared__ int s_last;
         if (tid == 0) {
@@ -852,78 +1044,82 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             p.tile_red[(int64_t)tile * 4 + 0] = a0;
             p.tile_red[(int64_t)tile * 4 + 1] = a1;
             p.tile_red[(int64_t)tile * 4 + 2] = a2;
-            __threadfence();
-            const unsigned old = atomicAdd(p.tile_counter, 1u);
-            s_last = (old == (unsigned)p.n_tiles - 1u);
+            s_last = 0;
+            if constexpr (OP == OP_ENERGY) {
+                __threadfence();
+                s_last = (atomicAdd(p.tile_counter, 1u) == (unsigned)p.n_tiles - 1u);
+            }
         }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            // per-thread Neumaier sums over a fixed strided subset, then a
-            // fixed combination order
-            double sum0 = 0, c0 = 0, sum1 = 0, c1 = 0, cnt = 0;
-            for (int t = tid; t < p.n_tiles; t += kThreads) {
-                const double x0 = __ldcg(p.tile_red + (int64_t)t * 4 + 0);
-                const double x1 = __ldcg(p.tile_red + (int64_t)t * 4 + 1);
-                cnt += __ldcg(p.tile_red + (int64_t)t * 4 + 2);
-                double tt = sum0 + x0;
-                c0 += (fabs(sum0) >= fabs(x0)) ? (sum0 - tt) + x0 : (x0 - tt) + sum0;
-                sum0 = tt;
-                tt = sum1 + x1;
-                c1 += (fabs(sum1) >= fabs(x1)) ? (sum1 - tt) + x1 : (x1 - tt) + sum1;
-                sum1 = tt;
-            }
-            double* red = sRed;
-            // warp butterfly on (sum, compensation) pairs, then warps in order
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double os = __shfl_xor_sync(0xffffffffu, sum0, o);
-                const double oc = __shfl_xor_sync(0xffffffffu, c0, o);
-                const double ps = __shfl_xor_sync(0xffffffffu, sum1, o);
-                const double pc = __shfl_xor_sync(0xffffffffu, c1, o);
-                const double ocnt = __shfl_xor_sync(0xffffffffu, cnt, o);
-                double tt = sum0 + os;
-                c0 += oc + ((fabs(sum0) >= fabs(os)) ? (sum0 - tt) + os : (os - tt) + sum0);
-                sum0 = tt;
-                tt = sum1 + ps;
-                c1 += pc + ((fabs(sum1) >= fabs(ps)) ? (sum1 - tt) + ps : (ps - tt) + sum1);
-                sum1 = tt;
-                cnt += ocnt;
-            }
+        if constexpr (OP == OP_ENERGY) {
             __syncthreads();
-            if (lane == 0) {
-                red[warp * 4 + 0] = sum0 + c0;
-                red[warp * 4 + 1] = sum1 + c1;
-                red[warp * 4 + 2] = cnt;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double S0 = 0, C0 = 0, S1 = 0, C1 = 0, N = 0;
-                for (int w = 0; w < kWarps; ++w) {
-                    double x = red[w * 4 + 0];
-                    double tt = S0 + x;
-                    C0 += (fabs(S0) >= fabs(x)) ? (S0 - tt) + x : (x - tt) + S0;
-                    S0 = tt;
-                    x = red[w * 4 + 1];
-                    tt = S1 + x;
-                    C1 += (fabs(S1) >= fabs(x)) ? (S1 - tt) + x : (x - tt) + S1;
-                    S1 = tt;
-                    N += red[w * 4 + 2];
-                }
-                if constexpr (OP == OP_ENERGY) {
-                    p.out_scalar[0] = N > 0 ? __longlong_as_double(0x7ff0000000000000ll) : S0 + C0;
-                    p.out_scalar[1] = S1 + C1;
+            if (s_last) {
+                __threadfence();
+                double S0 = 0, S1 = 0, N = 0;
+                reduce_tiles(p.tile_red, p.n_tiles, kThreads, sRed, S0, S1, N);
+                if (tid == 0) {
+                    p.out_scalar[0] = N > 0 ? __longlong_as_double(0x7ff0000000000000ll) : S0;
+                    p.out_scalar[1] = S1;
                     p.out_scalar[2] = N;
                     p.out_scalar[3] = 0.0;
-                } else if (p.out_scalar) {
-                    p.out_scalar[0] = S0 + C0;
+                    *p.tile_counter = 0u;
                 }
-                *p.tile_counter = 0u;
             }
         }
     }
     __syncthreads();
     if (tid == 0 && *sFlag) atomicOr(p.status, *sFlag);
+}
+
+// ---------------------------------------------------------------------------
+// finalize: each shared node's partial slots summed in slot order; nodes of
+// no element; the HVP's vKv from the tile partials
+// ---------------------------------------------------------------------------
+template <int D, typename T, int OP>
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) {
+    constexpr int VW = D == 2 ? 2 : 4;
+    constexpr int AW = (OP == OP_BLOCKDIAG) ? (D == 2 ? 4 : 6) : VW;
+    __shared__ double scratch[kFinThreads / 32 * 4];
+    grid_dependency_wait();  // the tile kernel's writes are visible past this point
+    const T* part = static_cast<const T*>(p.partial);
+    T* out = static_cast<T*>(p.out);
+    int fl = 0;
+    const int total = p.n_shared + p.n_orphans;
+    for (int j = blockIdx.x * kFinThreads + threadIdx.x; j < total; j += gridDim.x * kFinThreads) {
+        if (j < p.n_shared) {
+            const int64_t s0 = p.shared_slot_ptr[j], s1 = p.shared_slot_ptr[j + 1];
+            T sum[6] = {0, 0, 0, 0, 0, 0};
+            for (int64_t q = s0; q < s1; ++q) {
+                if constexpr (OP == OP_BLOCKDIAG) {
+#pragma unroll
+                    for (int c = 0; c < AW; ++c) sum[c] += part[q * AW + c];
+                } else {
+                    T t[4];
+                    lds_vec<VW, T>(part, (int)q, t);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) sum[c] += t[c];
+                }
+            }
+            const int g = p.shared_gid[j];
+            const uint8_t m = p.node_mask[g];
+            if constexpr (OP == OP_BLOCKDIAG)
+                fl |= write_block<D, T>(out, g, sum, m);
+            else
+                fl |= write_vec<D, T>(out, g, sum, m, p.flags);
+        } else {
+            const int g = p.orphans[j - p.n_shared];
+            const T zero[6] = {0, 0, 0, 0, 0, 0};
+            if constexpr (OP == OP_BLOCKDIAG)
+                write_block<D, T>(out, g, zero, (uint8_t)0x7);
+            else
+                write_vec<D, T>(out, g, zero, 0, 0u);
+        }
+    }
+    if (fl) atomicOr(p.status, fl);
+    if (OP == OP_HVP && p.out_scalar != nullptr && blockIdx.x == 0) {
+        double S0 = 0, S1 = 0, N = 0;
+        reduce_tiles(p.tile_red, p.n_tiles, kFinThreads, scratch, S0, S1, N);
+        if (threadIdx.x == 0) p.out_scalar[0] = S0;
+    }
 }
 
 }  // namespace fem

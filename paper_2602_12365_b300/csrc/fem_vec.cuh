@@ -1,0 +1,106 @@
+// Lane-vector arithmetic for the element kernels.
+//
+// V is the type one lane computes with: double (FP64 calls), float (FP32
+// calls, one element per lane) or F2 (FP32 calls, two elements per lane in
+// the two halves of a packed pair, evaluated with the sm_100+ paired FP32
+// instructions __ffma2_rn / __fadd2_rn / __fmul2_rn).  Every routine in
+// fem_material.cuh is written once against this interface.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fem {
+
+struct F2 {
+    float2 v;
+};
+
+__device__ __forceinline__ F2 mk2(float a, float b) { return F2{make_float2(a, b)}; }
+
+template <class V>
+struct VT;
+template <>
+struct VT<float> {
+    using S = float;
+    static constexpr int N = 1;
+};
+template <>
+struct VT<double> {
+    using S = double;
+    static constexpr int N = 1;
+};
+template <>
+struct VT<F2> {
+    using S = float;
+    static constexpr int N = 2;
+};
+
+template <class V>
+__device__ __forceinline__ V splat(typename VT<V>::S s);
+template <>
+__device__ __forceinline__ float splat<float>(float s) {
+    return s;
+}
+template <>
+__device__ __forceinline__ double splat<double>(double s) {
+    return s;
+}
+template <>
+__device__ __forceinline__ F2 splat<F2>(float s) {
+    return mk2(s, s);
+}
+
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+// a - b as b * (-1) + a: one rounding, identical to the scalar difference
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    return F2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)};
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2{__fmul2_rn(a.v, make_float2(-1.f, -1.f))}; }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) {
+    a = a + b;
+    return a;
+}
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) {
+    a = a - b;
+    return a;
+}
+
+// per-component scalar functions
+__device__ __forceinline__ float vrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double vrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ F2 vrcp(F2 x) { return mk2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+
+__device__ __forceinline__ float vlog1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double vlog1p(double x) { return log1p(x); }
+__device__ __forceinline__ F2 vlog1p(F2 x) { return mk2(log1pf(x.v.x), log1pf(x.v.y)); }
+
+__device__ __forceinline__ float vabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double vabs(double x) { return fabs(x); }
+__device__ __forceinline__ F2 vabs(F2 x) { return mk2(fabsf(x.v.x), fabsf(x.v.y)); }
+
+// bit c set when component c is > 0
+__device__ __forceinline__ int vpos(float x) { return x > 0.f ? 1 : 0; }
+__device__ __forceinline__ int vpos(double x) { return x > 0.0 ? 1 : 0; }
+__device__ __forceinline__ int vpos(F2 x) { return (x.v.x > 0.f ? 1 : 0) | (x.v.y > 0.f ? 2 : 0); }
+
+// keep components whose bit is set, replace the others by `alt`
+__device__ __forceinline__ float vsel(int bits, float x, float alt) { return (bits & 1) ? x : alt; }
+__device__ __forceinline__ double vsel(int bits, double x, double alt) { return (bits & 1) ? x : alt; }
+__device__ __forceinline__ F2 vsel(int bits, F2 x, float alt) {
+    return mk2((bits & 1) ? x.v.x : alt, (bits & 2) ? x.v.y : alt);
+}
+
+// component c as double (for FP64 accumulation)
+__device__ __forceinline__ double vget(float x, int) { return (double)x; }
+__device__ __forceinline__ double vget(double x, int) { return x; }
+__device__ __forceinline__ double vget(F2 x, int c) { return (double)(c ? x.v.y : x.v.x); }
+
+__device__ __forceinline__ float vcomp(float x, int) { return x; }
+__device__ __forceinline__ double vcomp(double x, int) { return x; }
+__device__ __forceinline__ float vcomp(F2 x, int c) { return c ? x.v.y : x.v.x; }
+
+}  // namespace fem

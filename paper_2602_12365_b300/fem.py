@@ -16,7 +16,7 @@ from . import _lib as L
 
 # CUDA kernels each C-ABI call launches (tile kernel, plus the finalize kernel
 # that sums the tile-shared nodes where there is one)
-KERNELS_PER_CALL = {"energy": 1, "residual": 1, "hvp": 1, "block_diag": 1, "param_vjp": 1}
+KERNELS_PER_CALL = {"energy": 1, "residual": 2, "hvp": 2, "block_diag": 2, "param_vjp": 1}
 
 
 def _ptr(t):
