@@ -139,12 +139,15 @@ fem_status fem_mesh_get_info(const fem_mesh* mesh, fem_mesh_info* info);
 
 /*
  * Host-only partition planner (no GPU needed): runs the same partitioner as
- * fem_mesh_create and returns, per element (HOST arrays, length n_elems, any
- * may be NULL), its tile, its global round (colour) id and its lane in the
- * round, plus the statistics.  Used to check the colouring on a CPU.
+ * fem_mesh_create and returns, per element (HOST arrays, any may be NULL), its
+ * tile, its global round (colour) id and its lane in the round
+ * ([n_elems] each), the element's node ids in the vertex order the kernels
+ * use ([n_elems * n_en]; P1 vertices may be reordered to avoid shared-memory
+ * bank conflicts), plus the statistics.  Used to check the plan on a CPU.
  */
 fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile,
-                              int64_t* elem_round, int32_t* elem_lane, fem_mesh_info* info);
+                              int64_t* elem_round, int32_t* elem_lane, int32_t* elem_nodes,
+                              fem_mesh_info* info);
 
 /*
  * fem_energy -- Psi_h(u) (Eq. 2) with per-element densities in the call's

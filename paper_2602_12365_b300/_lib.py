@@ -66,7 +66,7 @@ def lib():
             "fem_mesh_create": [C.POINTER(MeshDesc), C.POINTER(C.c_void_p), P],
             "fem_mesh_destroy": [P],
             "fem_mesh_get_info": [P, C.POINTER(MeshInfo)],
-            "fem_plan_partition": [C.POINTER(MeshDesc), P, P, P, C.POINTER(MeshInfo)],
+            "fem_plan_partition": [C.POINTER(MeshDesc), P, P, P, P, C.POINTER(MeshInfo)],
             "fem_energy": [P, i32, P, P, P],
             "fem_residual": [P, i32, P, P, u32, P],
             "fem_hvp": [P, i32, P, P, P, u32, P, P],

@@ -42,7 +42,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return LIB
     srcs = [os.path.join(CSRC, s) for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"),
+           "-Xcompiler", "-O2", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"),
            "-I", CSRC, "-o", LIB + ".tmp", *srcs, *(extra or [])]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)

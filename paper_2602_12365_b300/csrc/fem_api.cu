@@ -159,10 +159,54 @@ int elem_stride(int etype, bool mat) {
     return (n + 1) & ~1;
 }
 
+// P1 gradients and weight for the vertex order the kernel uses (any
+// permutation of the element's vertices): grad N_a from the rows of J^-1,
+// w det J from |det J| (an odd permutation flips the sign of det J).
+void p1_record_geometry(int D, const double* Xe, double* out /* (NEN-1)*D + 1 */) {
+    double g[4][3], wdJ;
+    double J[3][3] = {{0}};
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) J[i][j] = Xe[(j + 1) * D + i] - Xe[i];
+    double Ji[3][3], det;
+    if (D == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        Ji[0][0] = J[1][1] / det;
+        Ji[0][1] = -J[0][1] / det;
+        Ji[1][0] = -J[1][0] / det;
+        Ji[1][1] = J[0][0] / det;
+        wdJ = std::fabs(det) / 2.0;
+    } else {
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        Ji[0][0] = c00 / det;
+        Ji[1][0] = c01 / det;
+        Ji[2][0] = c02 / det;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        wdJ = std::fabs(det) / 6.0;
+    }
+    for (int k = 0; k < D; ++k) g[0][k] = 0.0;
+    for (int a = 1; a <= D; ++a)
+        for (int k = 0; k < D; ++k) {
+            g[a][k] = Ji[a - 1][k];
+            g[0][k] -= Ji[a - 1][k];
+        }
+    // the kernel takes the LAST vertex as reference: store grad N_0..N_{D-1}
+    for (int a = 0; a < D; ++a)
+        for (int k = 0; k < D; ++k) out[a * D + k] = g[a][k];
+    out[D * D] = wdJ;
+}
+
 template <typename T>
-void pack_records(fem_mesh* m, const fem_mesh_desc* d, const std::vector<double>& geo,
-                  std::vector<uint8_t>& out, int pi) {
+void pack_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out, int pi) {
     const fem::Plan& P = m->plan;
+    const int D = m->dim;
     const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
     const int conn_bytes = 2 * 32 * P.n_en_pad;
     const int stride = elem_stride(m->etype, m->per_elem_mat);
@@ -170,20 +214,28 @@ void pack_records(fem_mesh* m, const fem_mesh_desc* d, const std::vector<double>
     m->rec_bytes[pi] = RB;
     m->conn_bytes = conn_bytes;
     m->stride = stride;
-    const int64_t NR = P.n_rounds();
-    out.assign((size_t)(NR * RB), 0);
-    for (int64_t r = 0; r < NR; ++r) {
-        uint8_t* rec = out.data() + r * RB;
-        std::memcpy(rec, P.round_conn.data() + r * 32 * P.n_en_pad, conn_bytes);
-        T* el = reinterpret_cast<T*>(rec + conn_bytes);
-        for (int l = 0; l < 32; ++l) {
-            const int32_t e = P.round_elem[r * 32 + l];
-            if (e < 0) continue;
-            T* x = el + l * stride;
-            for (int k = 0; k < NG; ++k) x[k] = (T)geo[(size_t)e * NG + k];
-            if (m->per_elem_mat) {
-                x[NG] = (T)d->mu[e];
-                x[NG + 1] = (T)d->lambda[e];
+    out.assign((size_t)(P.n_rounds() * RB), 0);
+    double Xe[4 * 3], geo[10];
+    for (int t = 0; t < P.n_tiles(); ++t) {
+        const int32_t* gid = P.node_gid.data() + P.tile_node_ptr[t];
+        for (int64_t r = P.tile_round_ptr[t]; r < P.tile_round_ptr[t + 1]; ++r) {
+            uint8_t* rec = out.data() + r * RB;
+            std::memcpy(rec, P.round_conn.data() + r * 32 * P.n_en_pad, conn_bytes);
+            T* el = reinterpret_cast<T*>(rec + conn_bytes);
+            for (int l = 0; l < P.round_nvalid[r]; ++l) {
+                const int32_t e = P.round_elem[r * 32 + l];
+                T* x = el + l * stride;
+                if (NG) {
+                    const uint16_t* c = P.round_conn.data() + (r * 32 + l) * P.n_en_pad;
+                    for (int a = 0; a <= D; ++a)
+                        for (int k = 0; k < D; ++k) Xe[a * D + k] = d->coords[(size_t)gid[c[a]] * D + k];
+                    p1_record_geometry(D, Xe, geo);
+                    for (int k = 0; k < NG; ++k) x[k] = (T)geo[k];
+                }
+                if (m->per_elem_mat) {
+                    x[NG] = (T)d->mu[e];
+                    x[NG + 1] = (T)d->lambda[e];
+                }
             }
         }
     }
@@ -378,7 +430,7 @@ extern "C" {
 const char* fem_last_error(void) { return g_err.c_str(); }
 
 fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile, int64_t* elem_round,
-                              int32_t* elem_lane, fem_mesh_info* info) {
+                              int32_t* elem_lane, int32_t* elem_nodes, fem_mesh_info* info) {
     fem::Plan P;
     fem_status s = plan_from_desc(desc, P, desc ? desc->tile_elems : 0);
     if (s != FEM_OK) return s;
@@ -389,6 +441,10 @@ fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile, int
                 if (elem_tile) elem_tile[e] = t;
                 if (elem_round) elem_round[e] = r;
                 if (elem_lane) elem_lane[e] = l;
+                if (elem_nodes)
+                    for (int a = 0; a < P.n_en; ++a)
+                        elem_nodes[(int64_t)e * P.n_en + a] =
+                            P.node_gid[P.tile_node_ptr[t] + P.round_conn[((int64_t)r * 32 + l) * P.n_en_pad + a]];
             }
     if (info) fill_info(P, info);
     return FEM_OK;
@@ -430,11 +486,8 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
     const int D = m->dim, NEN = m->n_en;
     const int64_t NE = d->n_elems, NN = d->n_nodes;
 
-    // per-element geometry (P1) and orientation checks
-    std::vector<double> geo;
-    const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
-    if (NG) {
-        geo.assign((size_t)NE * NG, 0.0);
+    // orientation checks in the input vertex order
+    if (m->etype != 2) {
         double Xe[4 * 3], g[4][3], wdJ;
         for (int64_t e = 0; e < NE; ++e) {
             for (int a = 0; a < NEN; ++a)
@@ -443,10 +496,6 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
                 delete m;
                 return fail(FEM_ERR_BADMESH, "element " + std::to_string(e) + " has det J <= 0");
             }
-            // the kernel takes the LAST vertex as reference: store grad N_0..N_{NEN-2}
-            for (int a = 0; a < NEN - 1; ++a)
-                for (int k = 0; k < D; ++k) geo[(size_t)e * NG + a * D + k] = g[a][k];
-            geo[(size_t)e * NG + NG - 1] = wdJ;
         }
     } else {
         double Xe[24];
@@ -484,9 +533,9 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
         for (int pi = 0; pi < 2; ++pi) {
             if (pi == 1 && !mixed) break;
             if (pi == 0)
-                pack_records<double>(m, d, geo, recs, 0);
+                pack_records<double>(m, d, recs, 0);
             else
-                pack_records<float>(m, d, geo, recs, 1);
+                pack_records<float>(m, d, recs, 1);
             if ((s = upload(m, &m->rec[pi], recs.data(), recs.size(), st)) != FEM_OK) goto fail_out;
             if (m->etype == 2) {
                 if (pi == 0) {

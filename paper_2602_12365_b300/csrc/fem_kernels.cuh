@@ -36,9 +36,19 @@
 
 namespace fem {
 
-constexpr int kWarps = 4;
+// Tile shape (compile-time tuning knobs; the defaults are the measured best)
+#ifndef FEM_TILE_WARPS
+#define FEM_TILE_WARPS 4
+#endif
+#ifndef FEM_RING_STAGES
+#define FEM_RING_STAGES 3
+#endif
+#ifndef FEM_PAIR_FP32
+#define FEM_PAIR_FP32 1
+#endif
+constexpr int kWarps = FEM_TILE_WARPS;   // warps per tile (one accumulator copy each)
 constexpr int kThreads = 32 * kWarps;
-constexpr int kStages = 3;           // ring stages per warp
+constexpr int kStages = FEM_RING_STAGES;  // ring stages per warp
 constexpr int kSpinLimit = 1 << 20;  // bounded mbarrier waits
 constexpr int kFinThreads = 256;
 
@@ -61,7 +71,7 @@ struct ElemT<2> {  // Q1 hexahedron, 2x2x2 Gauss
 
 // rounds per warp iteration: FP32 P1 calls pack two rounds into FP32x2 pairs
 __host__ __device__ constexpr int rounds_per_iter(int et, int tsize) {
-    return (et != 2 && tsize == 4) ? 2 : 1;
+    return (FEM_PAIR_FP32 && et != 2 && tsize == 4) ? 2 : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -845,47 +855,48 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     // valid-lane counts of this warp's rounds, one per lane (at most 32 rounds)
     const int my_nv = (lane < my_n) ? p.round_nvalid[my_r0 + lane] : 0;
 
-    // 1. stage the tile's nodes; zero the accumulators
+    // 1. stage the tile's nodes; zero the accumulators.  Each thread issues
+    //    all of its loads (ids, then masks and nodal values) before any store,
+    //    so the gathers cost two memory round trips, not one per node.
     for (int base = 0; base < nl; base += 4 * kThreads) {
         int gid[4], slot[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = base + j * kThreads + tid;
-            gid[j] = (i < nl) ? p.node_gid[n0 + i] : 0;
+            gid[j] = (i < nl) ? p.node_gid[n0 + i] : -1;
             slot[j] = (i < nl) ? p.node_slot[n0 + i] : 0;
+        }
+        uint8_t msk[4];
+        T tu[4][4], tv[4][4], tx[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t g = gid[j] < 0 ? 0 : gid[j];
+            msk[j] = p.node_mask[g];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                tu[j][c] = (c < D) ? gu[g * D + c] : T(0);
+                if constexpr (kNeedV) tv[j][c] = (c < D) ? gv[g * D + c] : T(0);
+                if constexpr (ET == 2) tx[j][c] = (c < D) ? static_cast<const T*>(p.X)[g * D + c] : T(0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = base + j * kThreads + tid;
             if (i >= nl) continue;
-            const int64_t g = gid[j];
-            const uint8_t m = p.node_mask[g];
-            T t[4] = {0, 0, 0, 0};
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                t[c] = gu[g * D + c];
-                fin = fin && finite_(t[c]);
-            }
-            sts_vec<VW, T>(sU, i, t);
-            if constexpr (kNeedV) {
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    T x = gv[g * D + c];
-                    if (OP == OP_HVP && (p.flags & 2u) && ((m >> c) & 1)) x = T(0);
-                    fin = fin && finite_(x);
-                    t[c] = x;
+                fin = fin && finite_(tu[j][c]);
+                if constexpr (kNeedV) {
+                    if (OP == OP_HVP && (p.flags & 2u) && ((msk[j] >> c) & 1)) tv[j][c] = T(0);
+                    fin = fin && finite_(tv[j][c]);
                 }
-                sts_vec<VW, T>(sV, i, t);
             }
-            if constexpr (ET == 2) {
-                const T* gx = static_cast<const T*>(p.X);
-#pragma unroll
-                for (int c = 0; c < D; ++c) t[c] = gx[g * D + c];
-                sts_vec<VW, T>(sX, i, t);
-            }
+            sts_vec<VW, T>(sU, i, tu[j]);
+            if constexpr (kNeedV) sts_vec<VW, T>(sV, i, tv[j]);
+            if constexpr (ET == 2) sts_vec<VW, T>(sX, i, tx[j]);
             if (!fin) flags_local |= 2;
-            sMask[i] = m;
+            sMask[i] = msk[j];
             sGid[i] = gid[j];
             sSlot[i] = slot[j];
         }
@@ -915,7 +926,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         int valid = 0;
 #pragma unroll
         for (int h = 0; h < NR; ++h) {
-            const int nv = __shfl_sync(0xffffffffu, my_nv, (k0 + h) & 31);
+            int nv = __shfl_sync(0xffffffffu, my_nv, (k0 + h) & 31);
+            if (k0 + h >= 32 && k0 + h < my_n) nv = p.round_nvalid[my_r0 + k0 + h];
             const bool ok = (k0 + h < my_n) && lane < nv;
             valid |= ok ? (1 << h) : 0;
             read_half<ET, T>(st + h * p.rec_bytes, lane, ok, p, hs[h]);

@@ -29,6 +29,7 @@ struct MeshInput {
     const double* X = nullptr;
     const int32_t* conn = nullptr;
     int tile_elems = 0;
+    bool arrange = true;  // bank-conflict-free lane / vertex arrangement (P1)
 };
 
 struct Plan {
@@ -43,7 +44,9 @@ struct Plan {
     // rounds
     std::vector<int32_t> round_elem;      // [n_rounds*32] element id or -1
     std::vector<uint8_t> round_nvalid;    // [n_rounds]
-    std::vector<uint16_t> round_conn;     // [n_rounds*32*n_en_pad] local node ids
+    std::vector<uint16_t> round_conn;     // [n_rounds*32*n_en_pad] local node ids, in the
+                                          // vertex order the kernels use (P1: may differ
+                                          // from the input order; see round_elem)
     // shared nodes
     std::vector<int32_t> shared_gid;      // [n_shared]
     std::vector<int64_t> shared_slot_ptr; // [n_shared+1]

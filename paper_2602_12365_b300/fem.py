@@ -65,16 +65,18 @@ def make_desc(elem_type, coords, conn, mu=None, lam=None, mu0=1.0, lam0=10.0, di
 
 
 def plan_partition(elem_type, coords, conn, tile_elems=0):
-    """Host-only partition (no GPU): per element tile, round (colour), lane."""
+    """Host-only partition (no GPU): per element tile, round (colour), lane and
+    node ids in the vertex order the kernels use."""
     d, keep = make_desc(elem_type, coords, conn, tile_elems=tile_elems)
     ne = d.n_elems
     tile = np.zeros(ne, np.int32)
     rnd = np.zeros(ne, np.int64)
     lane = np.zeros(ne, np.int32)
+    nodes = np.zeros(keep["conn"].shape, np.int32)
     info = L.MeshInfo()
     L.check(L.lib().fem_plan_partition(C.byref(d), tile.ctypes.data, rnd.ctypes.data,
-                                       lane.ctypes.data, C.byref(info)))
-    return tile, rnd, lane, info.as_dict()
+                                       lane.ctypes.data, nodes.ctypes.data, C.byref(info)))
+    return tile, rnd, lane, nodes, info.as_dict()
 
 
 class Mesh:

@@ -45,21 +45,23 @@ def test_bad_descriptor_is_rejected_without_gpu(lib):
     conn[0, 0] = 10_000
     d, keep = make_desc(m.elem_type, m.coords, conn)
     info = lib.MeshInfo()
-    st = lib.lib().fem_plan_partition(C.byref(d), None, None, None, C.byref(info))
+    st = lib.lib().fem_plan_partition(C.byref(d), None, None, None, None, C.byref(info))
     assert st == 1  # FEM_ERR_ARG
     assert b"out of range" in lib.lib().fem_last_error()
-    st = lib.lib().fem_plan_partition(None, None, None, None, None)
+    st = lib.lib().fem_plan_partition(None, None, None, None, None, None)
     assert st == 1
 
 
-@pytest.mark.parametrize("kind,n,tile", [("tri", 24, 128), ("tet", 6, 200), ("tet", 9, 0),
+@pytest.mark.parametrize("kind,n,tile", [("tri", 24, 128), ("tri", 48, 0), ("tet", 6, 200), ("tet", 9, 0),
                                          ("hex", 7, 64), ("hex", 5, 0)])
 def test_two_level_colouring_is_valid(lib, kind, n, tile):
     from paper_2602_12365_b300.fem import plan_partition
     m = {"tri": lambda: mg.tri_mesh(n), "tet": lambda: mg.tet_mesh(n, jitter_seed=1),
          "hex": lambda: mg.hex_mesh(n)}[kind]()
-    tile_of, rnd, lane, info = plan_partition(m.elem_type, m.coords, m.conn, tile)
+    tile_of, rnd, lane, nodes, info = plan_partition(m.elem_type, m.coords, m.conn, tile)
     ne = m.n_el
+    # the kernel's vertex order is a permutation of each element's vertices
+    np.testing.assert_array_equal(np.sort(nodes, axis=1), np.sort(m.conn, axis=1))
     # every element exactly once: (round, lane) pairs are unique
     key = rnd * 32 + lane
     assert len(np.unique(key)) == ne
@@ -92,5 +94,5 @@ def test_plan_is_deterministic(lib):
     m = mg.tet_mesh(6, jitter_seed=3)
     a = plan_partition(m.elem_type, m.coords, m.conn, 128)
     b = plan_partition(m.elem_type, m.coords, m.conn, 128)
-    for x, y in zip(a[:3], b[:3]):
+    for x, y in zip(a[:4], b[:4]):
         np.testing.assert_array_equal(x, y)
