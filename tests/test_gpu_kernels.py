@@ -133,6 +133,34 @@ def test_bitwise_reproducible(case, dtype):
     assert torch.equal(r1, r2) and torch.equal(y1, y2) and torch.equal(e1, e2)
 
 
+@pytest.mark.parametrize("kind", ["tet", "tri"])
+def test_large_deformation_f32(kind):
+    """|J - 1| spans both sides of 3/8, where the FP32 logarithm switches from
+    its series to the library function."""
+    from paper_2602_12365_b300.fem import Mesh
+    m = mg.workload_tet(8, seed=1) if kind == "tet" else _jitter(mg.workload_tri(24), 0.2, 3)
+    gm = Mesh.from_fixture(m, tile_elems=128)
+    om = oracle.OracleMesh.from_mesh(m)
+    u = mg.smooth_state(m, 0.5, amp=0.07).ravel()
+    v = mg.random_direction(m, 2).ravel()
+    Xe = m.coords[m.conn]
+    ue = u.reshape(-1, m.dim)[m.conn]
+    if m.dim == 3:
+        J = np.linalg.det(np.linalg.solve(np.stack([Xe[:, k] - Xe[:, 3] for k in range(3)], 2).transpose(0, 2, 1),
+                                          np.stack([Xe[:, k] + ue[:, k] - Xe[:, 3] - ue[:, 3] for k in range(3)], 2).transpose(0, 2, 1)))
+    else:
+        J = np.linalg.det(np.linalg.solve(np.stack([Xe[:, k] - Xe[:, 2] for k in range(2)], 2).transpose(0, 2, 1),
+                                          np.stack([Xe[:, k] + ue[:, k] - Xe[:, 2] - ue[:, 2] for k in range(2)], 2).transpose(0, 2, 1)))
+    assert J.min() > 0 and np.abs(J - 1).max() > 0.375 and np.abs(J - 1).min() < 0.375
+    dt = torch.float32
+    ur, vr = _same(u, dt), _same(v, dt)
+    e = gm.energy(_t(u, dt)).cpu().numpy()
+    assert abs(e[0] - om.energy(ur)) <= 1e-5 * abs(om.energy(ur))
+    assert _rel(gm.residual(_t(u, dt)).cpu().numpy(), om.residual(ur)) <= 1e-5
+    assert _rel(gm.hvp(_t(u, dt), _t(v, dt)).cpu().numpy(), om.hvp(ur, vr)) <= 1e-5
+    assert gm.sync_status() == 0
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
