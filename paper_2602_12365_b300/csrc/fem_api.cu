@@ -14,6 +14,9 @@
 #include "fem_kernels.cuh"
 #include "fem_plan.h"
 
+static_assert(fem::kEmptyLane == fem::kNoNode, "kernel and planner agree on empty lanes");
+static_assert(fem::kNodeAlign % 16 == 0, "tile node lists must be bulk-copyable");
+
 namespace {
 thread_local std::string g_err;
 
@@ -50,6 +53,8 @@ struct fem_mesh {
     int64_t* shared_slot_ptr = nullptr;
     int32_t* orphans = nullptr;
     uint8_t* node_mask = nullptr;
+    uint8_t* node_mask_local = nullptr;
+    int max_nlp = 0;  // largest padded tile node count
     // element records per precision (index 0: FP64, 1: FP32)
     uint8_t* rec[2] = {nullptr, nullptr};
     int64_t rec_bytes[2] = {0, 0};
@@ -281,11 +286,17 @@ int record_bytes(int et, bool mat, int tsize) {
     return 2 * 32 * pad + tsize * 32 * elem_stride(et, mat);
 }
 
-int worst_smem(int et, int nl, bool mixed, bool mat) {
+int max_padded_nodes(const fem::Plan& P) {
+    int64_t w = 0;
+    for (int t = 0; t < P.n_tiles(); ++t) w = std::max(w, P.tile_node_ptr[t + 1] - P.tile_node_ptr[t]);
+    return (int)w;
+}
+
+int worst_smem(int et, int nlp, bool mixed, bool mat) {
     int w = 0;
     for (int op = 0; op < 5; ++op) {
-        w = std::max(w, fem::smem_layout(et, 8, op, nl, record_bytes(et, mat, 8)).total);
-        if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nl, record_bytes(et, mat, 4)).total);
+        w = std::max(w, fem::smem_layout(et, 8, op, nlp, record_bytes(et, mat, 8)).total);
+        if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nlp, record_bytes(et, mat, 4)).total);
     }
     return w;
 }
@@ -332,6 +343,8 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.orphans = m->orphans;
     p.n_orphans = (int)m->plan.orphans.size();
     p.node_mask = m->node_mask;
+    p.node_mask_local = m->node_mask_local;
+    p.max_nlp = m->max_nlp;
     p.X = m->X[pi];
     p.n_tiles = m->plan.n_tiles();
     p.mu0 = m->mu0;
@@ -347,9 +360,9 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_mu = out_mu;
     p.out_lam = out_lam;
     p.flags = flags;
-    const int smem =
-        fem::smem_layout(m->etype, tsize, op, m->plan.max_tile_nodes, (int)m->rec_bytes[pi]).total;
+    const int smem = fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi]).total;
     KFn fn = kernel_for(m->etype, dtype, op);
+    int grid = 0;
     {
         // raise the dynamic shared-memory limit once per (device, kernel)
         static std::mutex mu;
@@ -363,8 +376,20 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
             CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             set_to[key] = smem;
         }
+        // persistent grid: every resident slot, at most kMaxTilesPerCta tiles each
+        static std::map<std::pair<std::pair<int, const void*>, int>, int> resident;
+        auto rk = std::make_pair(key, smem);
+        auto ri = resident.find(rk);
+        if (ri == resident.end()) {
+            int per_sm = 0, sms = 0;
+            CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, fem::kThreads, smem));
+            CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            ri = resident.emplace(rk, std::max(1, per_sm) * sms).first;
+        }
+        grid = std::min(p.n_tiles, ri->second);
+        grid = std::max(grid, (p.n_tiles + fem::kMaxTilesPerCta - 1) / fem::kMaxTilesPerCta);
     }
-    fn<<<p.n_tiles, fem::kThreads, smem, st>>>(p);
+    fn<<<grid, fem::kThreads, smem, st>>>(p);
     CUDA_TRY(cudaGetLastError());
     if (op == fem::OP_RESIDUAL || op == fem::OP_HVP || op == fem::OP_BLOCKDIAG) {
         // shared nodes: programmatic dependent launch, so the launch overlaps
@@ -475,7 +500,7 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
             delete m;
             return s;
         }
-        if (worst_smem(m->etype, m->plan.max_tile_nodes, mixed, m->per_elem_mat) <= max_optin_smem()) break;
+        if (worst_smem(m->etype, max_padded_nodes(m->plan), mixed, m->per_elem_mat) <= max_optin_smem()) break;
         tile = m->plan.tile_elems / 2;
         if (tile < 32 || attempt > 6) {
             delete m;
@@ -527,6 +552,13 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
     UP(shared_slot_ptr, P.shared_slot_ptr);
     UP(orphans, P.orphans);
     UP(node_mask, mask);
+    {
+        std::vector<uint8_t> mloc(P.node_gid.size(), 0);
+        for (size_t j = 0; j < mloc.size(); ++j)
+            if (P.node_gid[j] >= 0) mloc[j] = mask[P.node_gid[j]];
+        UP(node_mask_local, mloc);
+    }
+    m->max_nlp = max_padded_nodes(P);
 #undef UP
     {
         std::vector<uint8_t> recs;

@@ -41,10 +41,10 @@ namespace fem {
 #define FEM_TILE_WARPS 4
 #endif
 #ifndef FEM_RING_STAGES
-#define FEM_RING_STAGES 3
+#define FEM_RING_STAGES 1
 #endif
 #ifndef FEM_PAIR_FP32
-#define FEM_PAIR_FP32 1
+#define FEM_PAIR_FP32 0
 #endif
 constexpr int kWarps = FEM_TILE_WARPS;   // warps per tile (one accumulator copy each)
 constexpr int kThreads = 32 * kWarps;
@@ -75,17 +75,24 @@ __host__ __device__ constexpr int rounds_per_iter(int et, int tsize) {
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory layout (bytes), identical on host and device
+// shared-memory layout (bytes), identical on host and device.  Two node
+// buffers (the current tile's and the next tile's: nodal u, v, X, node ids,
+// partial slots, Dirichlet bits), the per-warp accumulator copies, reduction
+// scratch, the CTA's tile table, the per-warp record ring and the mbarriers.
 // ---------------------------------------------------------------------------
+constexpr int kMaxTilesPerCta = 64;
+
 struct SmemLayout {
-    int off_u, off_v, off_x, off_acc, acc_bytes, off_mask, off_gid, off_slot, off_red, off_ring,
-        off_bar, total, aw, stage_bytes;
+    int off_u, off_v, off_x, off_gid, off_slot, off_mask, buf_bytes;  // inside one node buffer
+    int off_buf0, off_buf1, off_acc, acc_bytes, off_red, off_tab, off_ring, off_bar, total, aw,
+        stage_bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int align128(int x) { return (x + 127) & ~127; }
 
-__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nl, int rec_bytes) {
+// nlp: the largest padded tile node count
+__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nlp, int rec_bytes) {
     SmemLayout L;
     const int D = et == 0 ? 2 : 3;
     const int VW = D == 2 ? 2 : 4;
@@ -95,27 +102,33 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     const bool need_acc = (op == OP_RESIDUAL || op == OP_HVP || op == OP_BLOCKDIAG);
     int o = 0;
     L.off_u = o;
-    o = align16(o + nl * vec);
+    o = align16(o + nlp * vec);
     L.off_v = o;
-    if (need_v) o = align16(o + nl * vec);
+    if (need_v) o = align16(o + nlp * vec);
     L.off_x = o;
-    if (et == 2) o = align16(o + nl * vec);
-    L.off_acc = o;
-    L.acc_bytes = need_acc ? align16(kWarps * nl * L.aw * tsize) : 0;
-    o += L.acc_bytes;
+    if (et == 2) o = align16(o + nlp * vec);
     L.off_gid = o;
-    o = align16(o + nl * 4);
+    o = align16(o + nlp * 4);
     L.off_slot = o;
-    o = align16(o + nl * 4);
+    o = align16(o + nlp * 4);
     L.off_mask = o;
-    o = align16(o + nl);
+    o = align16(o + nlp);
+    L.buf_bytes = align128(o);
+    L.off_buf0 = 0;
+    L.off_buf1 = L.buf_bytes;
+    o = 2 * L.buf_bytes;
+    L.off_acc = o;
+    L.acc_bytes = need_acc ? align16(kWarps * nlp * L.aw * tsize) : 0;
+    o += L.acc_bytes;
     L.off_red = o;
     o = align16(o + kWarps * 4 * 8 + 16);
+    L.off_tab = o;
+    o = align16(o + kMaxTilesPerCta * 16);
     L.stage_bytes = rounds_per_iter(et, tsize) * rec_bytes;
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
     L.off_bar = o = align16(o);
-    o += kWarps * kStages * 8;
+    o += (kWarps * kStages + 2) * 8;
     L.total = align16(o);
     return L;
 }
@@ -141,9 +154,11 @@ struct KParams {
     int n_shared;
     const int32_t* orphans;
     int n_orphans;
-    const uint8_t* node_mask;
+    const uint8_t* node_mask;        // [n_nodes] Dirichlet bits
+    const uint8_t* node_mask_local;  // [n_local] Dirichlet bits per tile-local node
     const void* X;  // Q1: nodal coordinates [n_nodes][3] in the kernel's dtype
     int n_tiles;
+    int max_nlp;  // largest padded tile node count
     double mu0, lam0;
     // workspace
     void* partial;
@@ -209,6 +224,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// expect `bytes` on the barrier and arrive once (one per phase)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bulk copy that completes bytes on `bar` without arriving
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// asynchronous 4- or 8-byte global -> shared copies (completion by group)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void grid_dependency_wait() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -299,33 +339,40 @@ struct Half {
     T ed[NG + 2];  // geometry, mu, lambda
 };
 
+// Read lane's element of a round record (if the record is there and the lane
+// is not empty); returns whether it holds an element.  Empty lanes get node 0
+// and zero geometry so they compute harmlessly.
 template <int ET, typename T>
-__device__ __forceinline__ void read_half(const uint8_t* rec, int lane, bool valid, const KParams& p,
-                                          Half<ET, T>& h) {
+__device__ __forceinline__ bool read_half(const uint8_t* rec, int lane, bool present, const KParams& p,
+                                          T mu0, T lam0, Half<ET, T>& h) {
     using E = ElemT<ET>;
+    bool valid = false;
+    if (present) {
+        if constexpr (E::PAD == 4) {
+            const uint2 w = reinterpret_cast<const uint2*>(rec)[lane];
+            h.cn[0] = w.x & 0xffff;
+            h.cn[1] = w.x >> 16;
+            h.cn[2] = w.y & 0xffff;
+            if constexpr (E::NEN == 4) h.cn[3] = w.y >> 16;
+        } else {
+            const uint4 w = reinterpret_cast<const uint4*>(rec)[lane];
+            h.cn[0] = w.x & 0xffff;
+            h.cn[1] = w.x >> 16;
+            h.cn[2] = w.y & 0xffff;
+            h.cn[3] = w.y >> 16;
+            h.cn[4] = w.z & 0xffff;
+            h.cn[5] = w.z >> 16;
+            h.cn[6] = w.w & 0xffff;
+            h.cn[7] = w.w >> 16;
+        }
+        valid = h.cn[0] != 0xFFFF;
+    }
     if (!valid) {
 #pragma unroll
         for (int a = 0; a < E::NEN; ++a) h.cn[a] = 0;
 #pragma unroll
         for (int j = 0; j < E::NG + 2; ++j) h.ed[j] = T(0);
-        return;
-    }
-    if constexpr (E::PAD == 4) {
-        uint2 w = reinterpret_cast<const uint2*>(rec)[lane];
-        h.cn[0] = w.x & 0xffff;
-        h.cn[1] = w.x >> 16;
-        h.cn[2] = w.y & 0xffff;
-        if constexpr (E::NEN == 4) h.cn[3] = w.y >> 16;
-    } else {
-        uint4 w = reinterpret_cast<const uint4*>(rec)[lane];
-        h.cn[0] = w.x & 0xffff;
-        h.cn[1] = w.x >> 16;
-        h.cn[2] = w.y & 0xffff;
-        h.cn[3] = w.y >> 16;
-        h.cn[4] = w.z & 0xffff;
-        h.cn[5] = w.z >> 16;
-        h.cn[6] = w.w & 0xffff;
-        h.cn[7] = w.w >> 16;
+        return false;
     }
     const T* el = reinterpret_cast<const T*>(rec + p.conn_bytes) + lane * p.stride;
     if (p.has_mat) {
@@ -337,9 +384,10 @@ __device__ __forceinline__ void read_half(const uint8_t* rec, int lane, bool val
 #pragma unroll
             for (int j = 0; j < E::NG; ++j) h.ed[j] = g[j];
         }
-        h.ed[E::NG] = (T)p.mu0;
-        h.ed[E::NG + 1] = (T)p.lam0;
+        h.ed[E::NG] = mu0;
+        h.ed[E::NG + 1] = lam0;
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -800,8 +848,17 @@ __device__ __forceinline__ void reduce_tiles(const double* tile_red, int n_tiles
 }
 
 // ---------------------------------------------------------------------------
-// the tile kernel
+// the tile kernel (persistent: CTA c runs tiles c, c + G, c + 2G, ...)
+//
+// Per tile: [nodes of this tile ready: fix-ups, zero accumulators] -> rounds
+// (the records stream through the warp's ring, which runs ahead across tile
+// boundaries; after its first round each thread issues cp.async gathers of
+// the NEXT tile's nodal values into the other node buffer) -> combine and
+// write -> bulk copy of the node ids / slots / masks of the tile after next.
+// So a tile's node gathers overlap the previous tile's element work.
 // ---------------------------------------------------------------------------
+constexpr int kEmptyLane = 0xFFFF;  // local id of an empty lane (the planner's kNoNode)
+
 template <int ET, typename T, int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     using E = ElemT<ET>;
@@ -812,269 +869,328 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
     extern __shared__ __align__(128) unsigned char smem[];
 
-    const int tile = blockIdx.x;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
+    if (n_my == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t n0 = p.tile_node_ptr[tile];
-    const int nl = (int)(p.tile_node_ptr[tile + 1] - n0);
-    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, nl, p.rec_bytes);
+    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes);
     const int AW = L.aw;
-    T* sU = reinterpret_cast<T*>(smem + L.off_u);
-    T* sV = reinterpret_cast<T*>(smem + L.off_v);
-    T* sX = reinterpret_cast<T*>(smem + L.off_x);
     T* sAcc = reinterpret_cast<T*>(smem + L.off_acc);
-    int32_t* sGid = reinterpret_cast<int32_t*>(smem + L.off_gid);
-    int32_t* sSlot = reinterpret_cast<int32_t*>(smem + L.off_slot);
-    uint8_t* sMask = smem + L.off_mask;
     double* sRed = reinterpret_cast<double*>(smem + L.off_red);
     int* sFlag = reinterpret_cast<int*>(smem + L.off_red + kWarps * 4 * 8);
+    int4* tab = reinterpret_cast<int4*>(smem + L.off_tab);  // (node begin, padded count, round begin, rounds)
     uint8_t* ring = smem + L.off_ring + warp * kStages * L.stage_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp * kStages;
+    uint64_t* rbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp * kStages;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + kWarps * kStages;  // [2]
+    auto buf = [&](int b) { return smem + (b ? L.off_buf1 : L.off_buf0); };
 
     const T* gu = static_cast<const T*>(p.u);
     const T* gv = static_cast<const T*>(p.v);
+    const T* gx = static_cast<const T*>(p.X);
+    const T mu0 = (T)p.mu0, lam0 = (T)p.lam0;
     int flags_local = 0;
 
-    // 0. this warp's contiguous range of the tile's rounds; start its copies
-    const int r_begin = p.tile_round_ptr[tile], R = p.tile_round_ptr[tile + 1] - r_begin;
-    const int my_r0 = r_begin + warp * (R / kWarps) + min(warp, R % kWarps);
-    const int my_n = R / kWarps + (warp < R % kWarps ? 1 : 0);
-    const int n_it = (my_n + NR - 1) / NR;
-    if (lane == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    // 0. tile table and barriers
+    for (int i = tid; i < n_my; i += kThreads) {
+        const int t = cta + i * G;
+        const int64_t n0 = p.tile_node_ptr[t], n1 = p.tile_node_ptr[t + 1];
+        const int r0 = p.tile_round_ptr[t], r1 = p.tile_round_ptr[t + 1];
+        tab[i] = make_int4((int)n0, (int)(n1 - n0), r0, r1 - r0);
+    }
+    if (tid == 0) {
+        for (int k = 0; k < kWarps * kStages + 2; ++k)
+            mbar_init(reinterpret_cast<uint64_t*>(smem + L.off_bar) + k, 1);
+        *sFlag = 0;
         fence_mbar_init();
     }
-    __syncwarp();
-    auto issue = [&](int it) {
-        const int r = my_r0 + it * NR;
-        const int nrec = min(NR, my_n - it * NR);
-        bulk_load(ring + (it % kStages) * L.stage_bytes, p.rec + (int64_t)r * p.rec_bytes,
-                  (uint32_t)(nrec * p.rec_bytes), &bars[it % kStages]);
-    };
-    if (lane == 0)
-        for (int it = 0; it < n_it && it < kStages; ++it) issue(it);
-    // valid-lane counts of this warp's rounds, one per lane (at most 32 rounds)
-    const int my_nv = (lane < my_n) ? p.round_nvalid[my_r0 + lane] : 0;
+    __syncthreads();
 
-    // 1. stage the tile's nodes; zero the accumulators.  Each thread issues
-    //    all of its loads (ids, then masks and nodal values) before any store,
-    //    so the gathers cost two memory round trips, not one per node.
-    for (int base = 0; base < nl; base += 4 * kThreads) {
-        int gid[4], slot[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = base + j * kThreads + tid;
-            gid[j] = (i < nl) ? p.node_gid[n0 + i] : -1;
-            slot[j] = (i < nl) ? p.node_slot[n0 + i] : 0;
+    // node ids / slots / Dirichlet bits of tile i into buffer i & 1 (one thread)
+    auto issue_meta = [&](int i) {
+        const int4 tb = tab[i];
+        unsigned char* B = buf(i & 1);
+        uint64_t* bar = &mbar[i & 1];
+        mbar_arrive_expect_tx(bar, (uint32_t)(tb.y * 9));
+        bulk_copy(B + L.off_gid, p.node_gid + tb.x, (uint32_t)(tb.y * 4), bar);
+        bulk_copy(B + L.off_slot, p.node_slot + tb.x, (uint32_t)(tb.y * 4), bar);
+        bulk_copy(B + L.off_mask, p.node_mask_local + tb.x, (uint32_t)tb.y, bar);
+    };
+    // gather tile i's nodal values into buffer i & 1 (all threads, cp.async)
+    auto gather = [&](int i) {
+        const int b = i & 1;
+        if (!mbar_wait_bounded(&mbar[b], (uint32_t)((i >> 1) & 1))) {
+            flags_local |= 4;
+            return;
         }
-        uint8_t msk[4];
-        T tu[4][4], tv[4][4], tx[4][4];
+        unsigned char* B = buf(b);
+        const int32_t* bgid = reinterpret_cast<const int32_t*>(B + L.off_gid);
+        T* bu = reinterpret_cast<T*>(B + L.off_u);
+        T* bv = reinterpret_cast<T*>(B + L.off_v);
+        T* bx = reinterpret_cast<T*>(B + L.off_x);
+        const int nlp = tab[i].y;
+        for (int j = tid; j < nlp; j += kThreads) {
+            const int64_t g = bgid[j];
+            if (g < 0) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t g = gid[j] < 0 ? 0 : gid[j];
-            msk[j] = p.node_mask[g];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                tu[j][c] = (c < D) ? gu[g * D + c] : T(0);
-                if constexpr (kNeedV) tv[j][c] = (c < D) ? gv[g * D + c] : T(0);
-                if constexpr (ET == 2) tx[j][c] = (c < D) ? static_cast<const T*>(p.X)[g * D + c] : T(0);
+            for (int c = 0; c < D; ++c) {
+                cp_async<sizeof(T)>(bu + j * VW + c, gu + g * D + c);
+                if constexpr (kNeedV) cp_async<sizeof(T)>(bv + j * VW + c, gv + g * D + c);
+                if constexpr (ET == 2) cp_async<sizeof(T)>(bx + j * VW + c, gx + g * D + c);
             }
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = base + j * kThreads + tid;
-            if (i >= nl) continue;
+        cp_async_commit();
+    };
+
+    // ring producer (lane 0 of each warp): the warp's iterations of its
+    // tiles, in order, kStages ahead of the consumer
+    auto my_range = [&](int i, int& r0, int& n) {
+        const int4 tb = tab[i];
+        const int R = tb.w;
+        r0 = tb.z + warp * (R / kWarps) + min(warp, R % kWarps);
+        n = R / kWarps + (warp < R % kWarps ? 1 : 0);
+    };
+    int pi = 0, pit = 0, p_r0 = 0, p_n = 0, p_slot = 0, issued = 0;
+    my_range(0, p_r0, p_n);
+    auto issue_next = [&]() {
+        while (pit * NR >= p_n) {  // next tile with rounds for this warp
+            if (++pi >= n_my) return;
+            pit = 0;
+            my_range(pi, p_r0, p_n);
+        }
+        const int nrec = min(NR, p_n - pit * NR);
+        bulk_load(ring + p_slot * L.stage_bytes, p.rec + (int64_t)(p_r0 + pit * NR) * p.rec_bytes,
+                  (uint32_t)(nrec * p.rec_bytes), &rbar[p_slot]);
+        p_slot = (p_slot + 1 == kStages) ? 0 : p_slot + 1;
+        ++pit;
+        ++issued;
+    };
+
+    // 1. start: metadata of the first two tiles, the ring, tile 0's gathers
+    if (tid == 0) {
+        issue_meta(0);
+        if (n_my > 1) issue_meta(1);
+    }
+    if (lane == 0)
+        for (int k = 0; k < kStages; ++k) issue_next();
+    gather(0);
+
+    int consumed = 0, c_slot = 0;
+    uint32_t c_phase = 0;
+    bool timed_out = false;
+    int inv = 0;
+    for (int i = 0; i < n_my; ++i) {
+        const int t = cta + i * G;
+        unsigned char* B = buf(i & 1);
+        T* sU = reinterpret_cast<T*>(B + L.off_u);
+        T* sV = reinterpret_cast<T*>(B + L.off_v);
+        T* sX = reinterpret_cast<T*>(B + L.off_x);
+        const int32_t* sGid = reinterpret_cast<const int32_t*>(B + L.off_gid);
+        const int32_t* sSlot = reinterpret_cast<const int32_t*>(B + L.off_slot);
+        const uint8_t* sMask = B + L.off_mask;
+        const int nlp = tab[i].y;
+
+        cp_async_wait_all();
+        __syncthreads();
+        // 2. fix-ups of the gathered values; zero the accumulators
+        for (int j = tid; j < nlp; j += kThreads) {
+            if (sGid[j] < 0) continue;
+            const uint8_t m = sMask[j];
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                fin = fin && finite_(tu[j][c]);
+                fin = fin && finite_(sU[j * VW + c]);
                 if constexpr (kNeedV) {
-                    if (OP == OP_HVP && (p.flags & 2u) && ((msk[j] >> c) & 1)) tv[j][c] = T(0);
-                    fin = fin && finite_(tv[j][c]);
+                    if (OP == OP_HVP && (p.flags & 2u) && ((m >> c) & 1)) sV[j * VW + c] = T(0);
+                    fin = fin && finite_(sV[j * VW + c]);
                 }
             }
-            sts_vec<VW, T>(sU, i, tu[j]);
-            if constexpr (kNeedV) sts_vec<VW, T>(sV, i, tv[j]);
-            if constexpr (ET == 2) sts_vec<VW, T>(sX, i, tx[j]);
             if (!fin) flags_local |= 2;
-            sMask[i] = msk[j];
-            sGid[i] = gid[j];
-            sSlot[i] = slot[j];
         }
-    }
-    if constexpr (kNeedAcc) {
-        int4* z = reinterpret_cast<int4*>(sAcc);
-        for (int j = tid; j < L.acc_bytes / 16; j += kThreads) z[j] = make_int4(0, 0, 0, 0);
-    }
-    if (tid == 0) *sFlag = 0;
-    __syncthreads();
+        if constexpr (kNeedAcc) {
+            int4* z = reinterpret_cast<int4*>(sAcc);
+            const int nz = align16(kWarps * nlp * AW * (int)sizeof(T)) / 16;
+            for (int j = tid; j < nz; j += kThreads) z[j] = make_int4(0, 0, 0, 0);
+        }
+        __syncthreads();
 
-    // 2. rounds
-    ScalarAcc acc;
-    T* myAcc = sAcc + (int64_t)warp * nl * AW;
-    int inv = 0;
-    bool timed_out = false;
-    int it = 0;
-    for (; it < n_it; ++it) {
-        const int s = it % kStages;
-        if (!mbar_wait_bounded(&bars[s], (uint32_t)((it / kStages) & 1))) {
-            timed_out = true;
-            break;
-        }
-        const int k0 = it * NR;
-        const uint8_t* st = ring + s * L.stage_bytes;
-        Half<ET, T> hs[NR];
-        int valid = 0;
+        // 3. rounds
+        int my_r0, my_n;
+        my_range(i, my_r0, my_n);
+        const int n_it = (my_n + NR - 1) / NR;
+        T* myAcc = sAcc + (int64_t)warp * nlp * AW;
+        ScalarAcc acc;
+        bool gathered = (i + 1 >= n_my);
+        for (int it = 0; it < n_it && !timed_out; ++it) {
+            const int s = c_slot;
+            if (!mbar_wait_bounded(&rbar[s], c_phase)) {
+                timed_out = true;
+                break;
+            }
+            ++consumed;
+            if (++c_slot == kStages) {
+                c_slot = 0;
+                c_phase ^= 1u;
+            }
+            const int k0 = it * NR;
+            const uint8_t* st = ring + s * L.stage_bytes;
+            Half<ET, T> hs[NR];
+            int valid = 0;
 #pragma unroll
-        for (int h = 0; h < NR; ++h) {
-            int nv = __shfl_sync(0xffffffffu, my_nv, (k0 + h) & 31);
-            if (k0 + h >= 32 && k0 + h < my_n) nv = p.round_nvalid[my_r0 + k0 + h];
-            const bool ok = (k0 + h < my_n) && lane < nv;
-            valid |= ok ? (1 << h) : 0;
-            read_half<ET, T>(st + h * p.rec_bytes, lane, ok, p, hs[h]);
-        }
-        __syncwarp();
-        if (lane == 0 && it + kStages < n_it) {
-            fence_proxy_async_smem();
-            issue(it + kStages);
-        }
-        V f[NEN][6];
-        // add half h of the lane's contributions into the warp's accumulator
-        auto scatter = [&](int h) {
+            for (int h = 0; h < NR; ++h) {
+                const bool ok = read_half<ET, T>(st + h * p.rec_bytes, lane, k0 + h < my_n, p, mu0, lam0, hs[h]);
+                valid |= ok ? (1 << h) : 0;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            if (!gathered) {  // the next tile's nodes, spread over all threads
+                gather(i + 1);
+                gathered = true;
+            }
+            V f[NEN][6];
+            auto scatter = [&](int h) {
 #pragma unroll
-            for (int a = 0; a < NEN; ++a) {
-                const int n = hs[h].cn[a];
+                for (int a = 0; a < NEN; ++a) {
+                    const int n = hs[h].cn[a];
+                    if constexpr (OP == OP_BLOCKDIAG) {
+#pragma unroll
+                        for (int c = 0; c < (D == 3 ? 6 : 3); ++c) myAcc[n * AW + c] += vcomp(f[a][c], h);
+                    } else {
+                        T cur[4];
+                        lds_vec<VW, T>(myAcc, n, cur);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) cur[c] += vcomp(f[a][c], h);
+                        sts_vec<VW, T>(myAcc, n, cur);
+                    }
+                }
+            };
+            if (valid) {
+                double gmu[2] = {0, 0}, glam[2] = {0, 0};
+                element_work<ET, T, OP, V>(hs, valid, sU, sV, sX, f, acc, gmu, glam, inv);
+                if constexpr (OP == OP_PVJP) {
+#pragma unroll
+                    for (int h = 0; h < NR; ++h)
+                        if (valid & (1 << h)) {
+                            const int e = p.round_elem[(int64_t)(my_r0 + k0 + h) * 32 + lane];
+                            if (p.out_mu) p.out_mu[e] = gmu[h];
+                            if (p.out_lam) p.out_lam[e] = glam[h];
+                        }
+                }
+                if constexpr (kNeedAcc)
+                    if (valid & 1) scatter(0);
+            }
+            if constexpr (NR == 2 && kNeedAcc) {
+                __syncwarp();  // round k0 lands before round k0+1: they may share nodes
+                if (valid & 2) scatter(1);
+            }
+            __syncwarp();
+        }
+        if (!gathered && !timed_out) gather(i + 1);  // a warp without rounds in this tile
+
+        // 4. scalar partial of this tile (fixed order)
+        if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
+            double s0 = acc.s0, s1 = acc.s1, s2 = (double)acc.ninv;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            if (lane == 0) {
+                sRed[warp * 4 + 0] = s0;
+                sRed[warp * 4 + 1] = s1;
+                sRed[warp * 4 + 2] = s2;
+            }
+        }
+        __syncthreads();
+        if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
+            if (tid == 0 && (OP == OP_ENERGY || p.out_scalar != nullptr)) {
+                double a0 = 0, a1 = 0, a2 = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    a0 += sRed[w * 4 + 0];
+                    a1 += sRed[w * 4 + 1];
+                    a2 += sRed[w * 4 + 2];
+                }
+                p.tile_red[(int64_t)t * 4 + 0] = a0;
+                p.tile_red[(int64_t)t * 4 + 1] = a1;
+                p.tile_red[(int64_t)t * 4 + 2] = a2;
+            }
+        }
+
+        // 5. combine the warp copies; write private nodes and shared partials
+        if constexpr (kNeedAcc) {
+            T* part = static_cast<T*>(p.partial);
+            T* out = static_cast<T*>(p.out);
+            for (int j = tid; j < nlp; j += kThreads) {
+                const int g = sGid[j];
+                if (g < 0) continue;
+                T sum[6] = {0, 0, 0, 0, 0, 0};
                 if constexpr (OP == OP_BLOCKDIAG) {
 #pragma unroll
-                    for (int c = 0; c < (D == 3 ? 6 : 3); ++c) myAcc[n * AW + c] += vcomp(f[a][c], h);
+                    for (int w = 0; w < kWarps; ++w)
+                        for (int c = 0; c < AW; ++c) sum[c] += sAcc[((int64_t)w * nlp + j) * AW + c];
                 } else {
-                    T cur[4];
-                    lds_vec<VW, T>(myAcc, n, cur);
 #pragma unroll
-                    for (int c = 0; c < D; ++c) cur[c] += vcomp(f[a][c], h);
-                    sts_vec<VW, T>(myAcc, n, cur);
+                    for (int w = 0; w < kWarps; ++w) {
+                        T tv[4];
+                        lds_vec<VW, T>(sAcc + (int64_t)w * nlp * VW, j, tv);
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) sum[c] += tv[c];
+                    }
+                }
+                const int slot = sSlot[j];
+                if (slot < 0) {
+                    if constexpr (OP == OP_BLOCKDIAG)
+                        flags_local |= write_block<D, T>(out, g, sum, sMask[j]);
+                    else
+                        flags_local |= write_vec<D, T>(out, g, sum, sMask[j], p.flags);
+                } else if constexpr (OP == OP_BLOCKDIAG) {
+                    for (int c = 0; c < AW; ++c) part[(int64_t)slot * AW + c] = sum[c];
+                } else {
+                    sts_vec<VW, T>(part, slot, sum);  // one node vector per slot
                 }
             }
-        };
-        if (valid) {
-            double gmu[2] = {0, 0}, glam[2] = {0, 0};
-            element_work<ET, T, OP, V>(hs, valid, sU, sV, sX, f, acc, gmu, glam, inv);
-            if constexpr (OP == OP_PVJP) {
-#pragma unroll
-                for (int h = 0; h < NR; ++h)
-                    if (valid & (1 << h)) {
-                        const int e = p.round_elem[(int64_t)(my_r0 + k0 + h) * 32 + lane];
-                        if (p.out_mu) p.out_mu[e] = gmu[h];
-                        if (p.out_lam) p.out_lam[e] = glam[h];
-                    }
-            }
-            if constexpr (kNeedAcc)
-                if (valid & 1) scatter(0);
         }
-        if constexpr (NR == 2 && kNeedAcc) {
-            __syncwarp();  // round k0 lands before round k0+1: they may share nodes
-            if (valid & 2) scatter(1);
+        __syncthreads();
+        // 6. buffer i & 1 is free: bring in the metadata of tile i + 2
+        if (tid == 0 && i + 2 < n_my) {
+            fence_proxy_async_smem();
+            issue_meta(i + 2);
         }
-        __syncwarp();
     }
-    if (timed_out) {
-        // drain the copies still in flight before the CTA may exit
-        flags_local |= 4;
-        if (lane == 0)
-            for (int j = it; j < n_it && j < it + kStages; ++j)
-                mbar_wait_bounded(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
-        __syncwarp();
-    }
+    if (timed_out) flags_local |= 4;
+    // drain the copies still in flight before the CTA may exit
+    if (lane == 0)
+        for (int j = consumed; j < issued; ++j)
+            mbar_wait_bounded(&rbar[j % kStages], (uint32_t)((j / kStages) & 1));
+    cp_async_wait_all();
     if (inv) flags_local |= 1;
-
-    // 3. block sums of the scalar accumulators (fixed order)
-    if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
-        double s0 = acc.s0, s1 = acc.s1, s2 = (double)acc.ninv;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (lane == 0) {
-            sRed[warp * 4 + 0] = s0;
-            sRed[warp * 4 + 1] = s1;
-            sRed[warp * 4 + 2] = s2;
-        }
-    }
     {
         const int wf = __reduce_or_sync(0xffffffffu, flags_local);
         if (lane == 0 && wf) atomicOr(sFlag, wf);
     }
-    __syncthreads();
 
-    // 4. combine the warp copies; write private nodes and shared partials
-    if constexpr (kNeedAcc) {
-        T* part = static_cast<T*>(p.partial);
-        T* out = static_cast<T*>(p.out);
-        int wflag = 0;
-        for (int i = tid; i < nl; i += kThreads) {
-            T sum[6] = {0, 0, 0, 0, 0, 0};
-            if constexpr (OP == OP_BLOCKDIAG) {
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w)
-                    for (int c = 0; c < AW; ++c) sum[c] += sAcc[((int64_t)w * nl + i) * AW + c];
-            } else {
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) {
-                    T t[4];
-                    lds_vec<VW, T>(sAcc + (int64_t)w * nl * VW, i, t);
-#pragma unroll
-                    for (int c = 0; c < VW; ++c) sum[c] += t[c];
-                }
-            }
-            const int slot = sSlot[i];
-            if (slot < 0) {
-                if constexpr (OP == OP_BLOCKDIAG)
-                    wflag |= write_block<D, T>(out, sGid[i], sum, sMask[i]);
-                else
-                    wflag |= write_vec<D, T>(out, sGid[i], sum, sMask[i], p.flags);
-            } else if constexpr (OP == OP_BLOCKDIAG) {
-                for (int c = 0; c < AW; ++c) part[(int64_t)slot * AW + c] = sum[c];
-            } else {
-                sts_vec<VW, T>(part, slot, sum);  // one node vector per slot
-            }
-        }
-        if (wflag) atomicOr(sFlag, wflag);
-    }
-
-    // 5. scalar tile partials; the energy's last tile reduces them in tile
-    //    order (the HVP's are reduced by finalize_kernel)
-    if (OP == OP_ENERGY || (OP == OP_HVP && p.out_scalar != nullptr)) {
+    // 7. energy: the last CTA reduces the tile partials in tile order
+    if constexpr (OP == OP_ENERGY) {
         __shared__ int s_last;
+        __syncthreads();
         if (tid == 0) {
-            double a0 = 0, a1 = 0, a2 = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                a0 += sRed[w * 4 + 0];
-                a1 += sRed[w * 4 + 1];
-                a2 += sRed[w * 4 + 2];
-            }
-            p.tile_red[(int64_t)tile * 4 + 0] = a0;
-            p.tile_red[(int64_t)tile * 4 + 1] = a1;
-            p.tile_red[(int64_t)tile * 4 + 2] = a2;
-            s_last = 0;
-            if constexpr (OP == OP_ENERGY) {
-                __threadfence();
-                s_last = (atomicAdd(p.tile_counter, 1u) == (unsigned)p.n_tiles - 1u);
-            }
+            __threadfence();
+            s_last = (atomicAdd(p.tile_counter, 1u) == (unsigned)G - 1u);
         }
-        if constexpr (OP == OP_ENERGY) {
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                double S0 = 0, S1 = 0, N = 0;
-                reduce_tiles(p.tile_red, p.n_tiles, kThreads, sRed, S0, S1, N);
-                if (tid == 0) {
-                    p.out_scalar[0] = N > 0 ? __longlong_as_double(0x7ff0000000000000ll) : S0;
-                    p.out_scalar[1] = S1;
-                    p.out_scalar[2] = N;
-                    p.out_scalar[3] = 0.0;
-                    *p.tile_counter = 0u;
-                }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double S0 = 0, S1 = 0, N = 0;
+            reduce_tiles(p.tile_red, p.n_tiles, kThreads, sRed, S0, S1, N);
+            if (tid == 0) {
+                p.out_scalar[0] = N > 0 ? __longlong_as_double(0x7ff0000000000000ll) : S0;
+                p.out_scalar[1] = S1;
+                p.out_scalar[2] = N;
+                p.out_scalar[3] = 0.0;
+                *p.tile_counter = 0u;
             }
         }
     }

@@ -464,7 +464,7 @@ void build_tile(const MeshInput& in, const int32_t* elems, int E, int pad, TileO
     out.rounds = R1;
     out.elem.assign((size_t)R1 * kRound, -1);
     out.nvalid.assign(R1, 0);
-    out.conn.assign((size_t)R1 * kRound * pad, 0);
+    out.conn.assign((size_t)R1 * kRound * pad, kNoNode);  // empty lanes hold kNoNode
     std::vector<std::vector<int>> members(R1);
     for (int i = 0; i < E; ++i) members[round_of[i]].push_back(i);
     std::vector<int> lane_elem, perm;
@@ -552,6 +552,8 @@ std::string build_plan(const MeshInput& in, Plan& P) {
         P.tile_round_ptr.push_back(P.tile_round_ptr.back() + o.rounds);
         for (int32_t g : o.gid) tiles_of_node[g]++;
         P.node_gid.insert(P.node_gid.end(), o.gid.begin(), o.gid.end());
+        // pad the tile's node list to kNodeAlign entries (bulk-copyable)
+        while (P.node_gid.size() % kNodeAlign) P.node_gid.push_back(-1);
         P.tile_node_ptr.push_back((int64_t)P.node_gid.size());
         o = TileOut();  // release the tile's buffers
     }
@@ -572,6 +574,7 @@ std::string build_plan(const MeshInput& in, Plan& P) {
     P.node_slot.assign(P.node_gid.size(), -1);
     for (int t = 0; t < nt; ++t)
         for (int64_t j = P.tile_node_ptr[t]; j < P.tile_node_ptr[t + 1]; ++j) {
+            if (P.node_gid[j] < 0) continue;  // padding
             int32_t s = sid_of[P.node_gid[j]];
             if (s < 0) continue;
             int64_t slot = P.shared_slot_ptr[s] + fill[s]++;

@@ -21,6 +21,8 @@ namespace fem {
 
 constexpr int kRound = 32;       // elements per round (one per lane)
 constexpr int kMaxRounds = 128;  // per tile (bit masks in the colourer)
+constexpr int kNodeAlign = 16;   // tile node lists are padded to this many entries
+constexpr uint16_t kNoNode = 0xFFFF;  // local id of an empty lane in a round
 
 struct MeshInput {
     int elem_type = 1;  // 0 tri3, 1 tet4, 2 hex8
@@ -38,9 +40,9 @@ struct Plan {
     int tile_elems = 0;
     // tiles
     std::vector<int32_t> tile_round_ptr;  // [n_tiles+1]
-    std::vector<int64_t> tile_node_ptr;   // [n_tiles+1]
-    std::vector<int32_t> node_gid;        // [n_local] global node id
-    std::vector<int32_t> node_slot;       // [n_local] -1: private, else partial slot
+    std::vector<int64_t> tile_node_ptr;   // [n_tiles+1], multiples of kNodeAlign
+    std::vector<int32_t> node_gid;        // [n_local] global node id, -1 = padding
+    std::vector<int32_t> node_slot;       // [n_local] -1: private or padding, else partial slot
     // rounds
     std::vector<int32_t> round_elem;      // [n_rounds*32] element id or -1
     std::vector<uint8_t> round_nvalid;    // [n_rounds]
