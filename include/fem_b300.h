@@ -160,6 +160,34 @@ fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile,
 fem_status fem_energy(fem_mesh* mesh, int dtype, const void* u, double* out_dev, void* stream);
 
 /*
+ * fem_energy_static -- fem_energy's result, bit for bit (same kernel, same
+ * summation order), from a call that allocates nothing and uses none of the
+ * handle's reduction workspace.  The paper has no counterpart: this is a
+ * deployment variant for callers that may not allocate device memory after
+ * start-up.  The energy reduction's arrival counter and per-tile partials live
+ * in one file-scope device array of fixed size (a 256-byte line for the
+ * counter, then FEM_STATIC_MAX_TILES x 4 doubles: 512 KiB + 256 B), one copy
+ * per device and process.
+ *   - A mesh with more than FEM_STATIC_MAX_TILES tiles (fem_mesh_info.n_tiles)
+ *     is rejected with FEM_ERR_ARG and a message naming both numbers; nothing
+ *     is enqueued.  At the default tile sizes the limit is 16.7M P1 or 8.4M Q1
+ *     elements.
+ *   - Each call enqueues, on `stream`, a 4-byte memset that zeroes the counter,
+ *     then the kernel; the partials need no clearing (each tile writes its own
+ *     before the last CTA reads them).
+ *   - Overlapping calls race: every handle on the device shares the one
+ *     array, so two calls in flight at once (two streams, two threads, two
+ *     handles) give wrong sums.  Order them on one stream or by events.
+ *   - The first call on each device does one-time host-side setup (looks up
+ *     the array's device address with cudaGetSymbolAddress, sets the kernel's
+ *     shared-memory limit, queries its occupancy); make that first call
+ *     outside any stream capture.
+ * Arguments, output and status bits as for fem_energy.
+ */
+#define FEM_STATIC_MAX_TILES 16384
+fem_status fem_energy_static(fem_mesh* mesh, int dtype, const void* u, double* out_dev, void* stream);
+
+/*
  * fem_residual -- r = grad Psi_h(u) (Eq. 1): per element P = dpsi/dF =
  * mu (F - F^-T) + lambda ln J F^-T, r_a += w detJ P grad N_a, scattered
  * deterministically.  flags & FEM_MASK_OUT zeroes prescribed components.

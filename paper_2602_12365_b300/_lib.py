@@ -68,6 +68,7 @@ def lib():
             "fem_mesh_get_info": [P, C.POINTER(MeshInfo)],
             "fem_plan_partition": [C.POINTER(MeshDesc), P, P, P, P, C.POINTER(MeshInfo)],
             "fem_energy": [P, i32, P, P, P],
+            "fem_energy_static": [P, i32, P, P, P],
             "fem_residual": [P, i32, P, P, u32, P],
             "fem_hvp": [P, i32, P, P, P, u32, P, P],
             "fem_block_diag": [P, i32, P, P, P],
@@ -89,5 +90,5 @@ def check(status: int):
 
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_plan_partition",
-            "fem_energy", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
+            "fem_energy", "fem_energy_static", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
             "fem_sync_status", "fem_last_error"]

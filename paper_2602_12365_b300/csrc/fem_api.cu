@@ -315,9 +315,45 @@ KFn finalize_for(int dim, int dtype, int op) {
     return dim == 2 ? pick_fin<2, float>(op) : pick_fin<3, float>(op);
 }
 
+// Module-scope scratch of fem_energy_static: one 256-byte line holding the
+// energy reduction's arrival counter, then FEM_STATIC_MAX_TILES tile partials
+// of 4 doubles.  One copy per device and process, zero at module load.
+constexpr size_t kStaticCounterBytes = 256;
+constexpr size_t kStaticScratchBytes = kStaticCounterBytes + (size_t)FEM_STATIC_MAX_TILES * 4 * sizeof(double);
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct ReductionScratch {
+    double* tile_red;
+    unsigned* counter;
+};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (cudaGetSymbolAddress with that device current).
+fem_status static_scratch(ReductionScratch* out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void* addr[kMaxDevices] = {};
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(FEM_ERR_ARG, "device ordinal out of range for static scratch");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* a = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+        if (e != cudaSuccess || !a)
+            return fail(FEM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                          cudaGetErrorString(e));
+        addr[dev] = a;
+    }
+    unsigned char* base = static_cast<unsigned char*>(addr[dev]);
+    out->counter = reinterpret_cast<unsigned*>(base);
+    out->tile_red = reinterpret_cast<double*>(base + kStaticCounterBytes);
+    return FEM_OK;
+}
+
 fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
                   double* out_scalar, double* out_mu, double* out_lam, unsigned flags,
-                  cudaStream_t st) {
+                  cudaStream_t st, const ReductionScratch* scratch = nullptr) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
     if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
@@ -350,8 +386,8 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.mu0 = m->mu0;
     p.lam0 = m->lam0;
     p.partial = m->partial;
-    p.tile_red = m->tile_red;
-    p.tile_counter = m->tile_counter;
+    p.tile_red = scratch ? scratch->tile_red : m->tile_red;
+    p.tile_counter = scratch ? scratch->counter : m->tile_counter;
     p.status = m->status;
     p.u = u;
     p.v = v;
@@ -633,6 +669,24 @@ fem_status fem_energy(fem_mesh* m, int dtype, const void* u, double* out_dev, vo
     if (!u || !out_dev) return fail(FEM_ERR_ARG, "null u or output");
     return launch(m, dtype, fem::OP_ENERGY, u, nullptr, nullptr, out_dev, nullptr, nullptr, 0,
                   static_cast<cudaStream_t>(stream));
+}
+
+fem_status fem_energy_static(fem_mesh* m, int dtype, const void* u, double* out_dev, void* stream) {
+    if (!m) return fail(FEM_ERR_ARG, "null mesh");
+    if (!u || !out_dev) return fail(FEM_ERR_ARG, "null u or output");
+    const int n_tiles = m->plan.n_tiles();
+    if (n_tiles > FEM_STATIC_MAX_TILES)
+        return fail(FEM_ERR_ARG, "fem_energy_static: the mesh has " + std::to_string(n_tiles) +
+                                     " tiles but the static scratch holds " + std::to_string(FEM_STATIC_MAX_TILES) +
+                                     "; use fem_energy or larger tiles");
+    ReductionScratch scr{};
+    fem_status s = static_scratch(&scr);
+    if (s != FEM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the arrival counter must start at zero; the tile partials are written
+    // before they are read
+    CUDA_TRY(cudaMemsetAsync(scr.counter, 0, sizeof(unsigned), st));
+    return launch(m, dtype, fem::OP_ENERGY, u, nullptr, nullptr, out_dev, nullptr, nullptr, 0, st, &scr);
 }
 
 fem_status fem_residual(fem_mesh* m, int dtype, const void* u, void* r, unsigned flags, void* stream) {

@@ -136,6 +136,14 @@ class Mesh:
         L.check(L.lib().fem_energy(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
         return out
 
+    def energy_static(self, u, out=None, stream=None):
+        """energy() through fem_energy_static: reduction scratch in a fixed
+        module-scope device array, no allocation; calls must not overlap."""
+        self._check_vec(u)
+        out = out if out is not None else torch.empty(4, dtype=torch.float64, device=u.device)
+        L.check(L.lib().fem_energy_static(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
     def residual(self, u, mask_out=True, out=None, stream=None):
         self._check_vec(u)
         out = out if out is not None else torch.empty_like(u)
