@@ -158,10 +158,11 @@ bool hex_positive(const double* Xe) {
 
 // Record of one round (one bulk copy): u16 conn[32][PAD] | T elem[32][stride],
 // elem = (grad N_0 .. grad N_{NEN-2}, w det J | mu, lambda), stride even.
+// scalars per element in a round record: P1 geometry (grad N of all but the
+// last vertex, then w det J), then (mu, lambda) when they vary per element
 int elem_stride(int etype, bool mat) {
     const int NG = etype == 0 ? 5 : (etype == 1 ? 10 : 0);
-    const int n = NG + (mat ? 2 : 0);
-    return (n + 1) & ~1;
+    return NG + (mat ? 2 : 0);
 }
 
 // P1 gradients and weight for the vertex order the kernel uses (any
@@ -226,20 +227,25 @@ void pack_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out
         for (int64_t r = P.tile_round_ptr[t]; r < P.tile_round_ptr[t + 1]; ++r) {
             uint8_t* rec = out.data() + r * RB;
             std::memcpy(rec, P.round_conn.data() + r * 32 * P.n_en_pad, conn_bytes);
-            T* el = reinterpret_cast<T*>(rec + conn_bytes);
+            // geometry in 16-byte chunks (CW scalars of every lane, lane-major),
+            // then one (mu, lambda) pair per lane
+            T* el0 = reinterpret_cast<T*>(rec + conn_bytes);
+            constexpr int CW = 16 / (int)sizeof(T);
             for (int l = 0; l < P.round_nvalid[r]; ++l) {
                 const int32_t e = P.round_elem[r * 32 + l];
-                T* x = el + l * stride;
                 if (NG) {
                     const uint16_t* c = P.round_conn.data() + (r * 32 + l) * P.n_en_pad;
                     for (int a = 0; a <= D; ++a)
                         for (int k = 0; k < D; ++k) Xe[a * D + k] = d->coords[(size_t)gid[c[a]] * D + k];
                     p1_record_geometry(D, Xe, geo);
-                    for (int k = 0; k < NG; ++k) x[k] = (T)geo[k];
+                    for (int k = 0; k * CW < NG; ++k) {
+                        const int w = std::min(CW, NG - k * CW);
+                        for (int j = 0; j < w; ++j) el0[32 * k * CW + l * w + j] = (T)geo[k * CW + j];
+                    }
                 }
                 if (m->per_elem_mat) {
-                    x[NG] = (T)d->mu[e];
-                    x[NG + 1] = (T)d->lambda[e];
+                    el0[32 * NG + 2 * l + 0] = (T)d->mu[e];
+                    el0[32 * NG + 2 * l + 1] = (T)d->lambda[e];
                 }
             }
         }

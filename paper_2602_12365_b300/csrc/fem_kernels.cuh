@@ -46,6 +46,9 @@ namespace fem {
 #ifndef FEM_PAIR_FP32
 #define FEM_PAIR_FP32 0
 #endif
+#ifndef FEM_DUAL_ROUNDS
+#define FEM_DUAL_ROUNDS 1
+#endif
 constexpr int kWarps = FEM_TILE_WARPS;   // warps per tile (one accumulator copy each)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kStages = FEM_RING_STAGES;  // ring stages per warp
@@ -69,9 +72,17 @@ struct ElemT<2> {  // Q1 hexahedron, 2x2x2 Gauss
     static constexpr int D = 3, NEN = 8, PAD = 8, NG = 0, VW = 4;
 };
 
-// rounds per warp iteration: FP32 P1 calls pack two rounds into FP32x2 pairs
-__host__ __device__ constexpr int rounds_per_iter(int et, int tsize) {
-    return (FEM_PAIR_FP32 && et != 2 && tsize == 4) ? 2 : 1;
+// rounds per warp iteration: FEM_PAIR_FP32 packs two FP32 P1 rounds into
+// FP32x2 pairs; FEM_DUAL_ROUNDS gives each lane two independent elements (one
+// per round) computed with scalar arithmetic, so that their dependency chains
+// interleave, and fetches the two round records in one copy (FP32 P1 energy
+// and residual; the HVP's larger node buffers leave no room for the second
+// record in shared memory without losing a resident CTA)
+__host__ __device__ constexpr int rounds_per_iter(int et, int tsize, int op) {
+    return (et != 2 && tsize == 4 &&
+            (FEM_PAIR_FP32 || (FEM_DUAL_ROUNDS && (op == OP_ENERGY || op == OP_RESIDUAL))))
+               ? 2
+               : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -124,7 +135,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     o = align16(o + kWarps * 4 * 8 + 16);
     L.off_tab = o;
     o = align16(o + kMaxTilesPerCta * 16);
-    L.stage_bytes = rounds_per_iter(et, tsize) * rec_bytes;
+    L.stage_bytes = rounds_per_iter(et, tsize, op) * rec_bytes;
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
     L.off_bar = o = align16(o);
@@ -300,33 +311,41 @@ __device__ __forceinline__ void sts_vec(T* base, int i, const T* in) {
     }
 }
 
-// lane's element data from a round record in shared memory
+// Lane's geometry from a round record in shared memory.  The N geometry
+// scalars of the round's 32 elements are stored in 16-byte chunks: chunk k
+// holds scalars [k CW, k CW + w) of every lane, lane-major (CW = 4 floats or
+// 2 doubles; w = CW except for the last chunk), so each chunk is one
+// conflict-free vector load per lane.
 template <typename T, int N>
-__device__ __forceinline__ void lds_elem(const T* src, int stride, T (&dst)[N]) {
-    if constexpr (sizeof(T) == 4) {
-        if (stride % 4 == 0) {
+__device__ __forceinline__ void lds_chunks(const T* el0, int lane, T (&dst)[N]) {
+    constexpr int CW = 16 / (int)sizeof(T);
+    static_assert(N % CW != 3, "a 3-wide chunk has no vector load");
 #pragma unroll
-            for (int k = 0; k < (N + 3) / 4; ++k) {
-                float4 t = reinterpret_cast<const float4*>(src)[k];
-                if (4 * k + 0 < N) dst[4 * k + 0] = t.x;
-                if (4 * k + 1 < N) dst[4 * k + 1] = t.y;
-                if (4 * k + 2 < N) dst[4 * k + 2] = t.z;
-                if (4 * k + 3 < N) dst[4 * k + 3] = t.w;
+    for (int k = 0; k * CW < N; ++k) {
+        const int w = (N - k * CW < CW) ? N - k * CW : CW;
+        const T* src = el0 + 32 * k * CW;
+        if constexpr (sizeof(T) == 4) {
+            if (w == 4) {
+                const float4 t = reinterpret_cast<const float4*>(src)[lane];
+                dst[4 * k + 0] = t.x;
+                dst[4 * k + 1] = t.y;
+                dst[4 * k + 2] = t.z;
+                dst[4 * k + 3] = t.w;
+            } else if (w == 2) {
+                const float2 t = reinterpret_cast<const float2*>(src)[lane];
+                dst[4 * k + 0] = t.x;
+                dst[4 * k + 1] = t.y;
+            } else {
+                dst[4 * k] = src[lane];
             }
-            return;
-        }
-#pragma unroll
-        for (int k = 0; k < (N + 1) / 2; ++k) {
-            float2 t = reinterpret_cast<const float2*>(src)[k];
-            if (2 * k + 0 < N) dst[2 * k + 0] = t.x;
-            if (2 * k + 1 < N) dst[2 * k + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < (N + 1) / 2; ++k) {
-            double2 t = reinterpret_cast<const double2*>(src)[k];
-            if (2 * k + 0 < N) dst[2 * k + 0] = t.x;
-            if (2 * k + 1 < N) dst[2 * k + 1] = t.y;
+        } else {
+            if (w == 2) {
+                const double2 t = reinterpret_cast<const double2*>(src)[lane];
+                dst[2 * k + 0] = t.x;
+                dst[2 * k + 1] = t.y;
+            } else {
+                dst[2 * k] = src[lane];
+            }
         }
     }
 }
@@ -374,16 +393,19 @@ __device__ __forceinline__ bool read_half(const uint8_t* rec, int lane, bool pre
         for (int j = 0; j < E::NG + 2; ++j) h.ed[j] = T(0);
         return false;
     }
-    const T* el = reinterpret_cast<const T*>(rec + p.conn_bytes) + lane * p.stride;
-    if (p.has_mat) {
-        lds_elem<T, E::NG + 2>(el, p.stride, h.ed);
-    } else {
-        if constexpr (E::NG > 0) {
-            T g[E::NG];
-            lds_elem<T, E::NG>(el, p.stride, g);
+    const T* el0 = reinterpret_cast<const T*>(rec + p.conn_bytes);
+    if constexpr (E::NG > 0) {
+        T g[E::NG];
+        lds_chunks<T, E::NG>(el0, lane, g);
 #pragma unroll
-            for (int j = 0; j < E::NG; ++j) h.ed[j] = g[j];
-        }
+        for (int j = 0; j < E::NG; ++j) h.ed[j] = g[j];
+    }
+    if (p.has_mat) {  // (mu, lambda) pairs after the geometry chunks
+        using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        const T2 m = reinterpret_cast<const T2*>(el0 + 32 * E::NG)[lane];
+        h.ed[E::NG] = m.x;
+        h.ed[E::NG + 1] = m.y;
+    } else {
         h.ed[E::NG] = mu0;
         h.ed[E::NG + 1] = lam0;
     }
@@ -416,9 +438,37 @@ __host__ __device__ constexpr double hex_dN(int a, int q, int j) {
 // ---------------------------------------------------------------------------
 // quadrature-point work, shared by P1 and Q1
 // ---------------------------------------------------------------------------
-struct ScalarAcc {
+// Per-lane partial sums of element scalars over a tile (s0: energy or vKv;
+// s1: the energy's roundoff scale; ninv: quadrature points with J <= 0).
+// FP64 calls add in double.  FP32 calls keep s0 as an unevaluated float pair
+// hi + lo updated by Knuth's TwoSum, an error-free transformation, so the pair
+// holds the lane's sum to about 2^-46 relative before it is widened to double
+// once per tile; s1, a magnitude estimate, is a plain float sum.
+template <typename T>
+struct ScalarAcc;
+template <>
+struct ScalarAcc<double> {
     double s0 = 0, s1 = 0;
     int ninv = 0;
+    __device__ __forceinline__ void add0(double x) { s0 += x; }
+    __device__ __forceinline__ void add1(double x) { s1 += x; }
+    __device__ __forceinline__ double total0() const { return s0; }
+    __device__ __forceinline__ double total1() const { return s1; }
+};
+template <>
+struct ScalarAcc<float> {
+    float hi = 0.f, lo = 0.f, s1 = 0.f;
+    int ninv = 0;
+    __device__ __forceinline__ void add0(float x) {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float ap = s - bp;
+        lo += (hi - ap) + (x - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ void add1(float x) { s1 += x; }
+    __device__ __forceinline__ double total0() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ double total1() const { return (double)s1; }
 };
 
 template <int D, class V>
@@ -440,8 +490,8 @@ __device__ __forceinline__ void outer_sum(const V (*du)[D], const V (*g)[D], int
 template <int OP, int D, int NM1, class V>
 __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D], const V (&g)[NM1][D],
                                         V wdJ, V mu, V lam, int valid, V (&f)[NM1 + 1][6],
-                                        ScalarAcc& acc, double (&gmu)[2], double (&glam)[2],
-                                        int& inv) {
+                                        ScalarAcc<typename VT<V>::S>& acc, bool scal, double (&gmu)[2],
+                                        double (&glam)[2], int& inv) {
     using S = typename VT<V>::S;
     constexpr int N = VT<V>::N;
     Kin<D, V> k;
@@ -456,32 +506,34 @@ __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D],
     if constexpr (OP == OP_ENERGY) {
         V psi, sc;
         density<D, V>(k, mu, lam, psi, sc);
-        const V a = wdJ * psi, b = wdJ * sc;
+        // select, not multiply: a lane without an element (degenerate Q1
+        // geometry) may carry a non-finite density
+        const V a = vsel(good, wdJ * psi, S(0)), b = vsel(good, wdJ * sc, S(0));
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            acc.s0 += vget(a, c);
-            acc.s1 += vget(b, c);
+            acc.add0(vcomp(a, c));
+            acc.add1(vcomp(b, c));
         }
     } else if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
+        // P and dP are linear in (mu, lambda): w detJ folds into the moduli
+        const V wmu = wdJ * mu, wlam = wdJ * lam;
         V P[D][D];
         if constexpr (OP == OP_RESIDUAL) {
-            stress<D, V>(H, k, mu, lam, P);
+            stress<D, V>(H, k, wmu, wlam, P);
         } else {
-            tangent<D, V>(dF, k, mu, lam, P);
-            V s = P[0][0] * dF[0][0];
+            tangent<D, V>(dF, k, wmu, wlam, P);
+            if (scal) {  // w detJ dP : dF
+                V e = P[0][0] * dF[0][0];
 #pragma unroll
-            for (int i = 0; i < D; ++i)
+                for (int i = 0; i < D; ++i)
 #pragma unroll
-                for (int j = 0; j < D; ++j)
-                    if (i + j > 0) s = vfma(P[i][j], dF[i][j], s);
-            const V e = wdJ * s;
+                    for (int j = 0; j < D; ++j)
+                        if (i + j > 0) e = vfma(P[i][j], dF[i][j], e);
+                e = vsel(good, e, S(0));
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc.s0 += vget(e, c);
+                for (int c = 0; c < N; ++c) acc.add0(vcomp(e, c));
+            }
         }
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) P[i][j] = P[i][j] * wdJ;
 #pragma unroll
         for (int a = 0; a < NM1; ++a)
 #pragma unroll
@@ -570,8 +622,8 @@ struct Packer<2, ET, T> {
 // element of a round pair / single: gather, compute, return contributions
 template <int ET, typename T, int OP, class V>
 __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, const T* sU, const T* sV,
-                                             const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc& acc,
-                                             double (&gmu)[2], double (&glam)[2], int& inv) {
+                                             const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc<T>& acc,
+                                             bool scal, double (&gmu)[2], double (&glam)[2], int& inv) {
     using E = ElemT<ET>;
     using S = typename VT<V>::S;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1, NG = E::NG;
@@ -641,7 +693,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
         for (int a = 0; a <= NM1; ++a)
 #pragma unroll
             for (int c = 0; c < 6; ++c) fq[a][c] = splat<V>(S(0));
-        qp_work<OP, D, NM1, V>(H, dF, g, wdJ, mu, lam, valid, fq, acc, gmu, glam, inv);
+        qp_work<OP, D, NM1, V>(H, dF, g, wdJ, mu, lam, valid, fq, acc, scal, gmu, glam, inv);
         if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -727,7 +779,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
 #pragma unroll
                     for (int j = 0; j < D; ++j) dF[i][j] = splat<V>(S(0));
             }
-            qp_work<OP, D, NM1, V>(H, dF, g, detJ, mu, lam, valid, fr, acc, gmu, glam, inv);
+            qp_work<OP, D, NM1, V>(H, dF, g, detJ, mu, lam, valid, fr, acc, scal, gmu, glam, inv);
         }
         if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll
@@ -863,8 +915,9 @@ template <int ET, typename T, int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     using E = ElemT<ET>;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW;
-    constexpr int NR = rounds_per_iter(ET, (int)sizeof(T));
-    using V = typename std::conditional<NR == 2, F2, T>::type;
+    constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP);
+    constexpr bool kPacked = (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4);
+    using V = typename std::conditional<kPacked, F2, T>::type;
     constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -888,6 +941,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const T* gv = static_cast<const T*>(p.v);
     const T* gx = static_cast<const T*>(p.X);
     const T mu0 = (T)p.mu0, lam0 = (T)p.lam0;
+    // the HVP's fused vKv only when the caller asked for it
+    const bool want_scalar = (OP == OP_ENERGY) || (OP == OP_HVP && p.out_scalar != nullptr);
     int flags_local = 0;
 
     // 0. tile table and barriers
@@ -1018,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         my_range(i, my_r0, my_n);
         const int n_it = (my_n + NR - 1) / NR;
         T* myAcc = sAcc + (int64_t)warp * nlp * AW;
-        ScalarAcc acc;
+        ScalarAcc<T> acc;
         bool gathered = (i + 1 >= n_my);
         for (int it = 0; it < n_it && !timed_out; ++it) {
             const int s = c_slot;
@@ -1049,49 +1104,69 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                 gather(i + 1);
                 gathered = true;
             }
-            V f[NEN][6];
+            // element contributions: f[h] for round k0 + h (scalar), or both
+            // rounds packed in f[0] (FP32x2 pairs)
+            constexpr int NF = kPacked ? 1 : NR;
+            V f[NF][NEN][6] = {};
+            auto fc = [&](int h, int a, int c) -> T {
+                if constexpr (kPacked)
+                    return vcomp(f[0][a][c], h);
+                else
+                    return (T)f[h][a][c];
+            };
             auto scatter = [&](int h) {
 #pragma unroll
                 for (int a = 0; a < NEN; ++a) {
                     const int n = hs[h].cn[a];
                     if constexpr (OP == OP_BLOCKDIAG) {
 #pragma unroll
-                        for (int c = 0; c < (D == 3 ? 6 : 3); ++c) myAcc[n * AW + c] += vcomp(f[a][c], h);
+                        for (int c = 0; c < (D == 3 ? 6 : 3); ++c) myAcc[n * AW + c] += fc(h, a, c);
                     } else {
                         T cur[4];
                         lds_vec<VW, T>(myAcc, n, cur);
 #pragma unroll
-                        for (int c = 0; c < D; ++c) cur[c] += vcomp(f[a][c], h);
+                        for (int c = 0; c < D; ++c) cur[c] += fc(h, a, c);
                         sts_vec<VW, T>(myAcc, n, cur);
                     }
                 }
             };
-            if (valid) {
-                double gmu[2] = {0, 0}, glam[2] = {0, 0};
-                element_work<ET, T, OP, V>(hs, valid, sU, sV, sX, f, acc, gmu, glam, inv);
-                if constexpr (OP == OP_PVJP) {
+            double gmu[NR][2] = {}, glam[NR][2] = {};
+            if constexpr (kPacked) {
+                if (valid) element_work<ET, T, OP, V>(hs, valid, sU, sV, sX, f[0], acc, want_scalar, gmu[0], glam[0], inv);
+            } else {
+                // warp-uniform: the round is present; lanes without an element
+                // compute on zero geometry and skip the scatter
 #pragma unroll
-                    for (int h = 0; h < NR; ++h)
-                        if (valid & (1 << h)) {
-                            const int e = p.round_elem[(int64_t)(my_r0 + k0 + h) * 32 + lane];
-                            if (p.out_mu) p.out_mu[e] = gmu[h];
-                            if (p.out_lam) p.out_lam[e] = glam[h];
-                        }
-                }
-                if constexpr (kNeedAcc)
-                    if (valid & 1) scatter(0);
+                for (int h = 0; h < NR; ++h)
+                    if (k0 + h < my_n)
+                        element_work<ET, T, OP, V>(&hs[h], (valid >> h) & 1, sU, sV, sX, f[NF == 1 ? 0 : h], acc,
+                                                   want_scalar, gmu[h], glam[h], inv);
             }
-            if constexpr (NR == 2 && kNeedAcc) {
-                __syncwarp();  // round k0 lands before round k0+1: they may share nodes
-                if (valid & 2) scatter(1);
+            if constexpr (OP == OP_PVJP) {
+#pragma unroll
+                for (int h = 0; h < NR; ++h)
+                    if (valid & (1 << h)) {
+                        const int e = p.round_elem[(int64_t)(my_r0 + k0 + h) * 32 + lane];
+                        const double gm = kPacked ? gmu[0][h] : gmu[h][0];
+                        const double gl = kPacked ? glam[0][h] : glam[h][0];
+                        if (p.out_mu) p.out_mu[e] = gm;
+                        if (p.out_lam) p.out_lam[e] = gl;
+                    }
+            }
+            if constexpr (kNeedAcc) {
+#pragma unroll
+                for (int h = 0; h < NR; ++h) {
+                    if (h > 0) __syncwarp();  // round k0+h-1 lands first: rounds may share nodes
+                    if (valid & (1 << h)) scatter(h);
+                }
             }
             __syncwarp();
         }
         if (!gathered && !timed_out) gather(i + 1);  // a warp without rounds in this tile
 
         // 4. scalar partial of this tile (fixed order)
-        if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
-            double s0 = acc.s0, s1 = acc.s1, s2 = (double)acc.ninv;
+        if ((OP == OP_ENERGY || OP == OP_HVP) && want_scalar) {
+            double s0 = acc.total0(), s1 = acc.total1(), s2 = (double)acc.ninv;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 s0 += __shfl_xor_sync(0xffffffffu, s0, o);
