@@ -226,6 +226,85 @@ fem_status fem_block_diag(fem_mesh* mesh, int dtype, const void* u, void* D, voi
 fem_status fem_param_vjp(fem_mesh* mesh, int dtype, const void* u, const void* a,
                          double* g_mu, double* g_lam, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Matrix-free Newton-CG load stepping (Sec. 6.3.1 and 6.6 solve the
+ * nonlinear problems by Newton-Krylov iterations on the residual and its
+ * directional derivative; the paper fixes no further detail, so the
+ * algorithm below is one fixed choice, shared step for step with the CPU
+ * oracle):
+ *   1. du_c = (s - s_prev) ubar on prescribed DOFs;
+ *   2. predictor: t = M K(u) (I - M) du_c, r0 = ||t||; PCG on
+ *      M K M du_f = -t to predictor_rtol r0; u += du_c + du_f; prescribed
+ *      entries set to s ubar;
+ *   3. Newton: r = M grad Psi(u), stop when ||r|| <= newton_rtol r0 (r0 =
+ *      ||r|| when t = 0); PCG on M K M d = -r from 0 to eta ||r||,
+ *      eta = min(eta_max, sqrt(||r|| / r0)), and on p^T K p <= 0 the current
+ *      iterate (d = P r at the first iteration); backtracking Armijo line
+ *      search on Psi (alpha = 1, 1/2, ... ls_max halvings; accept when
+ *      Psi(u + a d) <= Psi(u) + armijo_c a r^T d, or when |dPsi| <= 16 eps S
+ *      and the residual norm decreases, S the roundoff scale of fem_energy);
+ *   4. an inverted state after the predictor, a non-SPD diagonal block, a
+ *      failed line search or newton_max iterations restore u and bisect the
+ *      increment, at most max_bisect levels deep.
+ * M is the Dirichlet mask; the preconditioner P is block Jacobi (each nodal
+ * diagonal block of fem_block_diag inverted through its Cholesky factor).
+ * ------------------------------------------------------------------------ */
+#define FEM_PC_BLOCK_JACOBI 0
+
+typedef struct {
+    int32_t cg_dtype;      /* FEM_F64: the PCG, its HVPs and preconditioner in
+                              FP64; FEM_F32: those in FP32 on an FP32 shadow of
+                              u (mesh must be FEM_PREC_MIXED), dot products and
+                              norms still FP64.  u, the Newton residual and the
+                              line-search energies are FP64 in both modes.     */
+    int32_t precond;       /* FEM_PC_BLOCK_JACOBI                            */
+    double newton_rtol;    /* 1e-8                                           */
+    int32_t newton_max;    /* 50                                             */
+    int32_t ls_max;        /* 20                                             */
+    double eta_max;        /* 0.1                                            */
+    int64_t cg_max;        /* 0 = 10 * n_dofs                                */
+    double predictor_rtol; /* 1e-2                                           */
+    double armijo_c;       /* 1e-4                                           */
+    int32_t max_bisect;    /* 5                                              */
+    int32_t cg_batch;      /* CG iterations enqueued between host checks of
+                              the device-side stop flag (0 = 8); iterations
+                              past the stop are skipped on the device, so the
+                              result does not depend on it                   */
+} fem_newton_opts;
+
+typedef struct {
+    int32_t status;       /* fem_status of the step                          */
+    int32_t newton_iters; /* Newton iterations over all increments           */
+    int64_t cg_iters;     /* HVPs inside PCG (predictors included)           */
+    int32_t bisections;
+    int32_t ls_halvings;
+    double r0_norm;       /* reference norm of the last increment            */
+    double r_norm;        /* final residual norm                             */
+} fem_newton_stats;
+
+/* Fill *opts with the defaults listed above. */
+fem_status fem_newton_default_opts(fem_newton_opts* opts);
+
+/*
+ * fem_newton_step -- advance u from load factor s_prev to s (s >= s_prev).
+ *   u     DEVICE double[n_nodes * dim]: on entry the state at s_prev, its
+ *         prescribed entries equal to s_prev * ubar; on FEM_OK the converged
+ *         state at s.  On failure u holds the last attempt of the deepest
+ *         bisection (as the oracle leaves it).
+ *   ubar  DEVICE double[n_nodes * dim]: prescribed displacement at s = 1
+ *         (read on prescribed components only).
+ *   opts  NULL for the defaults.  stats: HOST, always filled.
+ * Unlike the element calls this one synchronises `stream` (the host decides
+ * on convergence and line-search acceptance), and its first call on a handle
+ * allocates the solver workspace (about 12 vectors and two block arrays),
+ * kept until fem_mesh_destroy; a first bisection adds one save vector per
+ * level.  The handle's status word is left as it was on entry.
+ * Returns FEM_OK, FEM_ERR_INVERTED, FEM_ERR_NOT_SPD, FEM_ERR_NOT_CONVERGED or
+ * FEM_ERR_LINESEARCH (after all bisections), FEM_ERR_ARG or FEM_ERR_CUDA.
+ */
+fem_status fem_newton_step(fem_mesh* mesh, double* u, const double* ubar, double s_prev, double s,
+                           const fem_newton_opts* opts, fem_newton_stats* stats, void* stream);
+
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */
 fem_status fem_sync_status(fem_mesh* mesh, void* stream, int32_t* flags);

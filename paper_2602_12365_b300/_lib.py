@@ -42,6 +42,25 @@ class MeshInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+FEM_PC_BLOCK_JACOBI = 0
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("cg_dtype", C.c_int32), ("precond", C.c_int32), ("newton_rtol", C.c_double),
+                ("newton_max", C.c_int32), ("ls_max", C.c_int32), ("eta_max", C.c_double),
+                ("cg_max", C.c_int64), ("predictor_rtol", C.c_double), ("armijo_c", C.c_double),
+                ("max_bisect", C.c_int32), ("cg_batch", C.c_int32)]
+
+
+class NewtonStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("newton_iters", C.c_int32), ("cg_iters", C.c_int64),
+                ("bisections", C.c_int32), ("ls_halvings", C.c_int32), ("r0_norm", C.c_double),
+                ("r_norm", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FemError(RuntimeError):
     def __init__(self, status, msg):
         self.status = status
@@ -74,6 +93,9 @@ def lib():
             "fem_block_diag": [P, i32, P, P, P],
             "fem_param_vjp": [P, i32, P, P, P, P, P],
             "fem_sync_status": [P, P, C.POINTER(i32)],
+            "fem_newton_default_opts": [C.POINTER(NewtonOpts)],
+            "fem_newton_step": [P, P, P, C.c_double, C.c_double, C.POINTER(NewtonOpts),
+                                C.POINTER(NewtonStats), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -91,4 +113,4 @@ def check(status: int):
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_plan_partition",
             "fem_energy", "fem_energy_static", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
-            "fem_sync_status", "fem_last_error"]
+            "fem_sync_status", "fem_newton_default_opts", "fem_newton_step", "fem_last_error"]

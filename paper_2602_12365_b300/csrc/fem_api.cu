@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fem_b300.h"
+#include "fem_internal.h"
 #include "fem_kernels.cuh"
 #include "fem_plan.h"
 
@@ -32,41 +33,6 @@ fem_status fail(fem_status s, const std::string& msg) {
             return fail(FEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 }  // namespace
-
-struct fem_mesh {
-    fem::Plan plan;
-    fem_mesh_info info{};
-    int etype = 0, dim = 0, n_en = 0, precision = 0;
-    bool per_elem_mat = false;
-    double mu0 = 1.0, lam0 = 10.0;
-    std::vector<void*> allocs;
-    int64_t bytes = 0;
-    // plan on the device
-    int32_t* tile_round_ptr = nullptr;
-    int64_t* tile_node_ptr = nullptr;
-    int32_t* node_gid = nullptr;
-    int32_t* node_slot = nullptr;
-    uint8_t* round_nvalid = nullptr;
-    int32_t* round_elem = nullptr;
-    int32_t* slot_owner = nullptr;
-    int32_t* shared_gid = nullptr;
-    int64_t* shared_slot_ptr = nullptr;
-    int32_t* orphans = nullptr;
-    uint8_t* node_mask = nullptr;
-    uint8_t* node_mask_local = nullptr;
-    int max_nlp = 0;  // largest padded tile node count
-    // element records per precision (index 0: FP64, 1: FP32)
-    uint8_t* rec[2] = {nullptr, nullptr};
-    int64_t rec_bytes[2] = {0, 0};
-    int conn_bytes = 0;
-    int stride = 0;
-    void* X[2] = {nullptr, nullptr};
-    // workspace
-    void* partial = nullptr;
-    double* tile_red = nullptr;
-    unsigned* tile_counter = nullptr;
-    int* status = nullptr;
-};
 
 namespace {
 
@@ -359,7 +325,7 @@ fem_status static_scratch(ReductionScratch* out) {
 
 fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
                   double* out_scalar, double* out_mu, double* out_lam, unsigned flags,
-                  cudaStream_t st, const ReductionScratch* scratch = nullptr) {
+                  cudaStream_t st, const ReductionScratch* scratch = nullptr, const int* skip = nullptr) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
     if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
@@ -395,6 +361,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.tile_red = scratch ? scratch->tile_red : m->tile_red;
     p.tile_counter = scratch ? scratch->counter : m->tile_counter;
     p.status = m->status;
+    p.skip = skip;
     p.u = u;
     p.v = v;
     p.out = out;
@@ -491,6 +458,15 @@ void fill_info(const fem::Plan& P, fem_mesh_info* info) {
 }
 
 }  // namespace
+
+namespace femi {
+fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
+
+fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
+                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip) {
+    return launch(m, dtype, op, u, v, out, out_scalar, nullptr, nullptr, flags, st, nullptr, skip);
+}
+}  // namespace femi
 
 extern "C" {
 
@@ -660,6 +636,7 @@ fail_out:
 fem_status fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaDeviceSynchronize();
+    femi::solver_free(m);
     free_all(m);
     delete m;
     return FEM_OK;

@@ -1,0 +1,62 @@
+// Internal interface between the C-ABI translation units: the mesh handle's
+// layout, the element-kernel launcher and the error channel.  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fem_b300.h"
+#include "fem_plan.h"
+
+namespace femi {
+struct SolverWork;  // Newton-CG workspace, created on first use (fem_solver.cu)
+}
+
+struct fem_mesh {
+    fem::Plan plan;
+    fem_mesh_info info{};
+    int etype = 0, dim = 0, n_en = 0, precision = 0;
+    bool per_elem_mat = false;
+    double mu0 = 1.0, lam0 = 10.0;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    // plan on the device
+    int32_t* tile_round_ptr = nullptr;
+    int64_t* tile_node_ptr = nullptr;
+    int32_t* node_gid = nullptr;
+    int32_t* node_slot = nullptr;
+    uint8_t* round_nvalid = nullptr;
+    int32_t* round_elem = nullptr;
+    int32_t* slot_owner = nullptr;
+    int32_t* shared_gid = nullptr;
+    int64_t* shared_slot_ptr = nullptr;
+    int32_t* orphans = nullptr;
+    uint8_t* node_mask = nullptr;
+    uint8_t* node_mask_local = nullptr;
+    int max_nlp = 0;  // largest padded tile node count
+    // element records per precision (index 0: FP64, 1: FP32)
+    uint8_t* rec[2] = {nullptr, nullptr};
+    int64_t rec_bytes[2] = {0, 0};
+    int conn_bytes = 0;
+    int stride = 0;
+    void* X[2] = {nullptr, nullptr};
+    // workspace
+    void* partial = nullptr;
+    double* tile_red = nullptr;
+    unsigned* tile_counter = nullptr;
+    int* status = nullptr;
+    // Newton-CG workspace (allocated by the first fem_newton_step)
+    femi::SolverWork* solver = nullptr;
+};
+
+namespace femi {
+// records `msg` as the calling thread's last error and returns `s`
+fem_status set_error(fem_status s, const std::string& msg);
+// enqueue one element-kernel call (fem::Op `op`) on `st`; when `skip` is a
+// device pointer, the kernels return at once if *skip is non-zero
+fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
+                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip);
+// frees the Newton-CG workspace of `m` (no-op without one)
+void solver_free(fem_mesh* m);
+}  // namespace femi

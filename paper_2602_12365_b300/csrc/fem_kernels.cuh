@@ -176,6 +176,7 @@ struct KParams {
     double* tile_red;
     unsigned* tile_counter;
     int* status;
+    const int* skip;  // device flag: the call does nothing when *skip != 0 (may be null)
     // call
     const void* u;
     const void* v;
@@ -925,6 +926,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const int G = gridDim.x, cta = blockIdx.x;
     const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
     if (n_my == 0) return;
+    if (p.skip != nullptr && *p.skip != 0) return;  // uniform: set by an earlier kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes);
     const int AW = L.aw;
@@ -1283,6 +1285,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) 
     constexpr int AW = (OP == OP_BLOCKDIAG) ? (D == 2 ? 4 : 6) : VW;
     __shared__ double scratch[kFinThreads / 32 * 4];
     grid_dependency_wait();  // the tile kernel's writes are visible past this point
+    if (p.skip != nullptr && *p.skip != 0) return;
     const T* part = static_cast<const T*>(p.partial);
     T* out = static_cast<T*>(p.out);
     int fl = 0;

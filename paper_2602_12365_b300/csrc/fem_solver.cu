@@ -1,0 +1,849 @@
+// Matrix-free Newton-CG load step on the device (fem_newton_step).
+//
+// The paper minimises the total potential with Newton-Krylov iterations
+// built on the residual and its directional derivative (Sec. 6.3.1, 6.6) and
+// leaves the details open; this driver fixes one algorithm, step for step
+// the same as the oracle's load step:
+//   1. du_c = (s - s_prev) ubar on prescribed DOFs.
+//   2. predictor t = M K(u) (I - M) du_c, r0 = ||t||; PCG on M K M du_f = -t
+//      to relative tolerance 1e-2; u += du_c + du_f; prescribed u = s ubar.
+//   3. Newton: r = M grad Psi(u); stop when ||r|| <= rtol r0; PCG on
+//      M K M d = -r from 0 to eta ||r||, eta = min(eta_max, sqrt(||r||/r0))
+//      (non-positive curvature: first iteration d = P r, later the current
+//      iterate); backtracking Armijo on Psi with the roundoff guard
+//      |dPsi| <= 16 eps S and ||r|| decreasing; u += alpha d.
+//   4. an inverted predictor, a failed line search, a non-SPD block or
+//      newton_max iterations restore u and bisect the increment.
+// The preconditioner is block Jacobi: each nodal diagonal block inverted
+// through its Cholesky factor.
+//
+// Precision: u, the Newton residual and the line-search energies are FP64
+// in every mode (a converged residual of 1e-8 r0 and energy differences near
+// the roundoff floor need it).  cg_dtype FEM_F32 runs the PCG -- its HVPs,
+// block diagonal, preconditioner and vectors -- in FP32 on an FP32 shadow of
+// u, with every dot product and norm accumulated in FP64.
+//
+// The PCG loop runs on the device: alpha, beta, the residual norm and a
+// `done` state live in device memory, every kernel of an iteration returns at
+// once when done is set, and the host enqueues iterations in batches and
+// reads done one batch behind, so the GPU never waits for the host inside a
+// solve.  Every reduction is a fixed-order FP64 sum (per-thread strided
+// sums, a warp butterfly, warps in order, blocks in order by the last block),
+// so results are bitwise reproducible for a given mesh and device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fem_b300.h"
+#include "fem_internal.h"
+#include "fem_kernels.cuh"
+
+namespace {
+
+constexpr int kVT = 256;          // threads of the vector kernels
+constexpr int kMaxRedBlocks = 1184;  // 8 per SM on 148 SMs
+
+// device-resident scalars of one PCG solve
+struct CgState {
+    double rz;    // res . z
+    double pq;    // p . K p (written by the HVP's fused reduction)
+    double rr;    // res . res
+    double tol;   // absolute tolerance on ||res||
+    double beta;
+    long long cg_max;
+    int done;     // 0 running, 1 converged, 2 non-positive curvature, 3 iteration cap
+    int k;        // iterations (HVPs) performed
+    unsigned counter;  // last-block arrival counter
+    int pad;
+};
+
+struct DotState {
+    double value;
+    unsigned counter;
+    int pad;
+};
+
+// ---------------------------------------------------------------------------
+// fixed-order block reduction of NV doubles; the total lands in thread 0
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_total(double (&v)[NV], double* sh /* [kVT/32 * NV] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kVT / 32; ++w)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] += sh[w * NV + k];
+}
+
+// Each block stores its partial sums; the last block to arrive adds the
+// partials in block order and returns true (its thread 0 holds the totals).
+template <int NV>
+__device__ __forceinline__ bool grid_total(double (&v)[NV], double* partial, unsigned* counter) {
+    __shared__ double sh[kVT / 32 * NV];
+    __shared__ int last;
+    block_total<NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = v[k];
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kVT)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) t[k] += __ldcg(partial + b * NV + k);
+    block_total<NV>(t, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = t[k];
+        *counter = 0u;
+    }
+    return true;
+}
+
+// z = Minv_n r for one node (D x D row-major block)
+template <int D, typename T>
+__device__ __forceinline__ void apply_block(const T* Minv, int64_t n, const T (&r)[3], T (&z)[3]) {
+    const T* M = Minv + n * D * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T s = M[i * D] * r[0];
+#pragma unroll
+        for (int j = 1; j < D; ++j) s += M[i * D + j] * r[j];
+        z[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG kernels (one node per thread, grid-stride)
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* res, T* z, T* p,
+                                               const T* Minv, CgState* st, double* partial) {
+    double v[2] = {0.0, 0.0};
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        T r[3] = {0, 0, 0}, zz[3];
+#pragma unroll
+        for (int c = 0; c < D; ++c) r[c] = b[n * D + c];
+        apply_block<D, T>(Minv, n, r, zz);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            x[n * D + c] = T(0);
+            res[n * D + c] = r[c];
+            z[n * D + c] = zz[c];
+            p[n * D + c] = zz[c];
+            v[0] += (double)r[c] * (double)r[c];
+            v[1] += (double)r[c] * (double)zz[c];
+        }
+    }
+    if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
+        st->rr = v[0];
+        st->rz = v[1];
+        st->k = 0;
+        st->done = (sqrt(v[0]) <= st->tol) ? 1 : 0;
+    }
+}
+
+// alpha = rz / pq; x += alpha p; res -= alpha q; z = Minv res; new rz, rr;
+// convergence test and beta by the last block
+template <int D, typename T>
+__global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z, const T* p, const T* q,
+                                                 const T* Minv, CgState* st, double* partial) {
+    if (st->done) return;  // uniform: only the last block of a kernel writes done
+    const double pq = st->pq, rz = st->rz;
+    const int k = st->k;
+    double v[2] = {0.0, 0.0};
+    if (!(pq > 0.0)) {
+        // non-positive curvature: stop; at the first iteration take d = P r
+        if (k == 0)
+            for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT)
+#pragma unroll
+                for (int c = 0; c < D; ++c) x[n * D + c] = z[n * D + c];
+        if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
+            st->k = k + 1;
+            st->done = 2;
+        }
+        return;
+    }
+    const T alpha = (T)(rz / pq);
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        T r[3] = {0, 0, 0}, zz[3];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            x[n * D + c] += alpha * p[n * D + c];
+            r[c] = res[n * D + c] - alpha * q[n * D + c];
+            res[n * D + c] = r[c];
+        }
+        apply_block<D, T>(Minv, n, r, zz);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            z[n * D + c] = zz[c];
+            v[0] += (double)r[c] * (double)r[c];
+            v[1] += (double)r[c] * (double)zz[c];
+        }
+    }
+    if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
+        const int k1 = k + 1;
+        st->k = k1;
+        st->rr = v[0];
+        if (sqrt(v[0]) <= st->tol) {
+            st->done = 1;
+        } else {
+            st->beta = v[1] / rz;
+            st->rz = v[1];
+            if (k1 >= st->cg_max) st->done = 3;
+        }
+    }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kVT) cg_pupdate(int64_t nn, T* p, const T* z, const CgState* st) {
+    if (st->done) return;
+    const T beta = (T)st->beta;
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < nn * D; i += (int64_t)gridDim.x * kVT)
+        p[i] = z[i] + beta * p[i];
+}
+
+// FP64 dot product a . b with a fixed summation order
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kVT) dot_kernel(int64_t n, const TA* a, const TB* b, DotState* ds,
+                                                  double* partial) {
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        v[0] += (double)a[i] * (double)b[i];
+    if (grid_total<1>(v, partial, &ds->counter) && threadIdx.x == 0) ds->value = v[0];
+}
+
+// ---------------------------------------------------------------------------
+// element-wise vector kernels
+// ---------------------------------------------------------------------------
+// du = (s1 - s0) ubar on prescribed DOFs, 0 elsewhere (FP64 and, if asked, FP32)
+template <int D>
+__global__ void predictor_increment(int64_t nn, const uint8_t* mask, const double* ubar, double ds,
+                                    double* du, float* du32) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        const uint8_t m = mask[n];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double v = ((m >> c) & 1) ? ds * ubar[n * D + c] : 0.0;
+            du[n * D + c] = v;
+            if (du32) du32[n * D + c] = (float)v;
+        }
+    }
+}
+
+__global__ void to_f32(int64_t n, const double* a, float* b) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        b[i] = (float)a[i];
+}
+
+template <typename TS, typename TD>
+__global__ void negate(int64_t n, const TS* a, TD* b) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        b[i] = -(TD)a[i];
+}
+
+// u += du on prescribed DOFs, u += x elsewhere
+template <int D, typename T>
+__global__ void apply_predictor(int64_t nn, const uint8_t* mask, double* u, const double* du, const T* x) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        const uint8_t m = mask[n];
+#pragma unroll
+        for (int c = 0; c < D; ++c) u[n * D + c] += ((m >> c) & 1) ? du[n * D + c] : (double)x[n * D + c];
+    }
+}
+
+template <int D>
+__global__ void set_prescribed(int64_t nn, const uint8_t* mask, double* u, const double* ubar, double s) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        const uint8_t m = mask[n];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if ((m >> c) & 1) u[n * D + c] = s * ubar[n * D + c];
+    }
+}
+
+// ut = u + alpha x
+template <typename T>
+__global__ void trial_point(int64_t n, const double* u, double alpha, const T* x, double* ut) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        ut[i] = u[i] + alpha * (double)x[i];
+}
+
+// Minv_n = D_n^-1 through the Cholesky factor D_n = L L^T (FP64 per node):
+// L^-1 by forward substitution, Minv = L^-T L^-1.  A non-positive pivot sets
+// *bad and leaves the identity.
+template <int D, typename T>
+__global__ void block_jacobi_inverse(int64_t nn, const T* Db, T* Minv, int* bad) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        double A[D][D], L[D][D] = {}, Li[D][D] = {};
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) A[i][j] = (double)Db[n * D * D + i * D + j];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                double s = A[i][j];
+#pragma unroll
+                for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+                if (i == j) {
+                    if (!(s > 0.0)) {
+                        ok = false;
+                        s = 1.0;
+                    }
+                    L[i][i] = sqrt(s);
+                } else {
+                    L[i][j] = s / L[j][j];
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < i; ++k) s -= L[i][k] * Li[k][j];
+                Li[i][j] = s / L[i][i];
+            }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += Li[k][i] * Li[k][j];
+                Minv[n * D * D + i * D + j] = ok ? (T)s : (T)(i == j ? 1.0 : 0.0);
+            }
+        if (!ok) atomicOr(bad, 1);
+    }
+}
+
+int grid_for(int64_t work) {
+    const int64_t g = (work + kVT - 1) / kVT;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+}
+
+fem_status fail(fem_status s, const std::string& msg) { return femi::set_error(s, msg); }
+
+#define CUDA_TRY(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(FEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define FEM_TRY(call)                      \
+    do {                                   \
+        fem_status s_ = (call);            \
+        if (s_ != FEM_OK) return s_;       \
+    } while (0)
+
+}  // namespace
+
+namespace femi {
+
+struct SolverWork {
+    int64_t nn = 0, nd = 0;
+    int D = 0;
+    std::vector<void*> allocs;
+    // FP64 vectors
+    double *r = nullptr, *t = nullptr, *du = nullptr, *ut = nullptr;
+    std::vector<double*> saves;  // one per bisection depth
+    float *u32 = nullptr, *du32 = nullptr;
+    // CG vectors, index 0: FP64, 1: FP32 (allocated on first use)
+    void *b[2] = {}, *x[2] = {}, *res[2] = {}, *z[2] = {}, *p[2] = {}, *q[2] = {}, *Minv[2] = {},
+         *Db[2] = {};
+    double* partial = nullptr;
+    CgState* cg = nullptr;
+    DotState* dot = nullptr;
+    double* scal = nullptr;  // energy output (4 doubles)
+    int* bad = nullptr;
+    // pinned host mirror
+    struct Host {
+        CgState cg;
+        DotState dot;
+        double scal[4];
+        int done[2];
+        int bad;
+        int status;
+    }* h = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+void solver_free(fem_mesh* m) {
+    SolverWork* w = m ? m->solver : nullptr;
+    if (!w) return;
+    for (void* p : w->allocs) cudaFree(p);
+    for (double* p : w->saves) cudaFree(p);
+    if (w->h) cudaFreeHost(w->h);
+    for (auto& e : w->ev)
+        if (e) cudaEventDestroy(e);
+    delete w;
+    m->solver = nullptr;
+}
+
+}  // namespace femi
+
+namespace {
+
+using femi::SolverWork;
+
+template <typename T>
+fem_status dalloc(SolverWork* w, T** p, size_t n) {
+    void* q = nullptr;
+    CUDA_TRY(cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)));
+    w->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return FEM_OK;
+}
+
+fem_status ensure_work(fem_mesh* m, int cg_dtype) {
+    if (!m->solver) {
+        auto* w = new SolverWork();
+        m->solver = w;
+        w->nn = m->info.n_nodes;
+        w->D = m->dim;
+        w->nd = w->nn * w->D;
+        FEM_TRY(dalloc(w, &w->r, w->nd));
+        FEM_TRY(dalloc(w, &w->t, w->nd));
+        FEM_TRY(dalloc(w, &w->du, w->nd));
+        FEM_TRY(dalloc(w, &w->ut, w->nd));
+        FEM_TRY(dalloc(w, &w->partial, (size_t)kMaxRedBlocks * 2));
+        FEM_TRY(dalloc(w, &w->cg, 1));
+        FEM_TRY(dalloc(w, &w->dot, 1));
+        FEM_TRY(dalloc(w, &w->scal, 4));
+        FEM_TRY(dalloc(w, &w->bad, 1));
+        CUDA_TRY(cudaMemset(w->cg, 0, sizeof(CgState)));
+        CUDA_TRY(cudaMemset(w->dot, 0, sizeof(DotState)));
+        void* h = nullptr;
+        CUDA_TRY(cudaMallocHost(&h, sizeof(SolverWork::Host)));
+        w->h = static_cast<SolverWork::Host*>(h);
+        std::memset(w->h, 0, sizeof(SolverWork::Host));
+        for (auto& e : w->ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    SolverWork* w = m->solver;
+    const int pi = cg_dtype == FEM_F64 ? 0 : 1;
+    if (!w->b[pi]) {
+        const size_t ts = pi == 0 ? 8 : 4;
+        void** vecs[] = {&w->b[pi], &w->x[pi], &w->res[pi], &w->z[pi], &w->p[pi], &w->q[pi]};
+        for (void** v : vecs) {
+            uint8_t* q = nullptr;
+            FEM_TRY(dalloc(w, &q, (size_t)w->nd * ts));
+            *v = q;
+        }
+        uint8_t* q = nullptr;
+        FEM_TRY(dalloc(w, &q, (size_t)w->nn * w->D * w->D * ts));
+        w->Minv[pi] = q;
+        FEM_TRY(dalloc(w, &q, (size_t)w->nn * w->D * w->D * ts));
+        w->Db[pi] = q;
+        if (pi == 1) {
+            FEM_TRY(dalloc(w, &w->u32, w->nd));
+            FEM_TRY(dalloc(w, &w->du32, w->nd));
+        }
+    }
+    return FEM_OK;
+}
+
+// One load increment and its bisection; mirrors the oracle step for step.
+class Stepper {
+public:
+    Stepper(fem_mesh* m, const fem_newton_opts& o, fem_newton_stats* stats, cudaStream_t st)
+        : m_(m), o_(o), stats_(stats), st_(st), w_(m->solver), D_(m->dim) {
+        dt_ = o.cg_dtype;
+        pi_ = dt_ == FEM_F64 ? 0 : 1;
+        cg_max_ = o.cg_max > 0 ? o.cg_max : 10 * w_->nd;
+    }
+
+    // returns 0 on success or the oracle's failure code (3 inverted, 5 not
+    // SPD, 6 not converged, 7 line search); a CUDA failure sets *err
+    int step_rec(double* u, const double* ubar, double s0, double s1, int depth, fem_status* err) {
+        if ((int)w_->saves.size() <= depth) {
+            double* sv = nullptr;
+            if (cudaMalloc(&sv, sizeof(double) * w_->nd) != cudaSuccess) {
+                *err = fail(FEM_ERR_CUDA, "cudaMalloc of a bisection save vector failed");
+                return -1;
+            }
+            w_->saves.push_back(sv);
+        }
+        double* save = w_->saves[depth];
+        if (cudaMemcpyAsync(save, u, sizeof(double) * w_->nd, cudaMemcpyDeviceToDevice, st_) != cudaSuccess) {
+            *err = fail(FEM_ERR_CUDA, "cudaMemcpyAsync (save) failed");
+            return -1;
+        }
+        int rc = increment(u, ubar, s0, s1, err);
+        if (*err != FEM_OK) return -1;
+        if (rc != 0 && depth < o_.max_bisect) {
+            if (cudaMemcpyAsync(u, save, sizeof(double) * w_->nd, cudaMemcpyDeviceToDevice, st_) != cudaSuccess) {
+                *err = fail(FEM_ERR_CUDA, "cudaMemcpyAsync (restore) failed");
+                return -1;
+            }
+            stats_->bisections++;
+            const double sm = 0.5 * (s0 + s1);
+            rc = step_rec(u, ubar, s0, sm, depth + 1, err);
+            if (rc == 0 && *err == FEM_OK) rc = step_rec(u, ubar, sm, s1, depth + 1, err);
+        }
+        return rc;
+    }
+
+private:
+    fem_mesh* m_;
+    fem_newton_opts o_;
+    fem_newton_stats* stats_;
+    cudaStream_t st_;
+    SolverWork* w_;
+    int D_, dt_, pi_;
+    int64_t cg_max_;
+
+    int grid_nodes() const { return grid_for(w_->nn); }
+    int grid_dofs() const { return grid_for(w_->nd); }
+
+    fem_status sync() {
+        CUDA_TRY(cudaStreamSynchronize(st_));
+        return FEM_OK;
+    }
+
+    // FP64 dot a . b (ta, tb: FEM_F64 / FEM_F32), returned to the host
+    fem_status dot(const void* a, int ta, const void* b, int tb, double* out) {
+        const int g = grid_dofs();
+        const int64_t n = w_->nd;
+        if (ta == FEM_F64 && tb == FEM_F64)
+            dot_kernel<double, double><<<g, kVT, 0, st_>>>(n, (const double*)a, (const double*)b, w_->dot, w_->partial);
+        else if (ta == FEM_F64)
+            dot_kernel<double, float><<<g, kVT, 0, st_>>>(n, (const double*)a, (const float*)b, w_->dot, w_->partial);
+        else if (tb == FEM_F64)
+            dot_kernel<float, double><<<g, kVT, 0, st_>>>(n, (const float*)a, (const double*)b, w_->dot, w_->partial);
+        else
+            dot_kernel<float, float><<<g, kVT, 0, st_>>>(n, (const float*)a, (const float*)b, w_->dot, w_->partial);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(&w_->h->dot, w_->dot, sizeof(DotState), cudaMemcpyDeviceToHost, st_));
+        FEM_TRY(sync());
+        *out = w_->h->dot.value;
+        return FEM_OK;
+    }
+
+    // Psi(u) and the roundoff scale S (FP64)
+    fem_status energy(const double* u, double* psi, double* S) {
+        FEM_TRY(femi::run_op(m_, FEM_F64, fem::OP_ENERGY, u, nullptr, nullptr, w_->scal, 0, st_, nullptr));
+        CUDA_TRY(cudaMemcpyAsync(w_->h->scal, w_->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st_));
+        FEM_TRY(sync());
+        *psi = w_->h->scal[0];
+        *S = w_->h->scal[1];
+        return FEM_OK;
+    }
+
+    fem_status residual(const double* u, double* r) {
+        return femi::run_op(m_, FEM_F64, fem::OP_RESIDUAL, u, nullptr, r, nullptr, FEM_MASK_OUT, st_, nullptr);
+    }
+
+    // the state the CG's element kernels see: u itself (FP64) or its FP32 shadow
+    const void* cg_state(const double* u) {
+        if (pi_ == 0) return u;
+        to_f32<<<grid_dofs(), kVT, 0, st_>>>(w_->nd, u, w_->u32);
+        return w_->u32;
+    }
+
+    // block-Jacobi preconditioner at u; returns 5 when a block is not SPD
+    int build_block_jacobi(const void* ucg, fem_status* err) {
+        *err = femi::run_op(m_, dt_, fem::OP_BLOCKDIAG, ucg, nullptr, w_->Db[pi_], nullptr, 0, st_, nullptr);
+        if (*err != FEM_OK) return -1;
+        if (cudaMemsetAsync(w_->bad, 0, sizeof(int), st_) != cudaSuccess) {
+            *err = fail(FEM_ERR_CUDA, "cudaMemsetAsync failed");
+            return -1;
+        }
+        const int g = grid_nodes();
+        if (D_ == 2) {
+            if (pi_ == 0)
+                block_jacobi_inverse<2, double><<<g, kVT, 0, st_>>>(w_->nn, (const double*)w_->Db[0], (double*)w_->Minv[0], w_->bad);
+            else
+                block_jacobi_inverse<2, float><<<g, kVT, 0, st_>>>(w_->nn, (const float*)w_->Db[1], (float*)w_->Minv[1], w_->bad);
+        } else {
+            if (pi_ == 0)
+                block_jacobi_inverse<3, double><<<g, kVT, 0, st_>>>(w_->nn, (const double*)w_->Db[0], (double*)w_->Minv[0], w_->bad);
+            else
+                block_jacobi_inverse<3, float><<<g, kVT, 0, st_>>>(w_->nn, (const float*)w_->Db[1], (float*)w_->Minv[1], w_->bad);
+        }
+        if (cudaMemcpyAsync(&w_->h->bad, w_->bad, sizeof(int), cudaMemcpyDeviceToHost, st_) != cudaSuccess ||
+            cudaStreamSynchronize(st_) != cudaSuccess) {
+            *err = fail(FEM_ERR_CUDA, "block-Jacobi readback failed");
+            return -1;
+        }
+        return w_->h->bad ? 5 : 0;
+    }
+
+    template <int D, typename T>
+    fem_status launch_cg_iteration(const void* ucg) {
+        SolverWork* w = w_;
+        const int pi = pi_;
+        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->p[pi], w->q[pi], &w->cg->pq, FEM_MASK_IN | FEM_MASK_OUT,
+                             st_, &w->cg->done));
+        cg_update<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
+                                                      (const T*)w->p[pi], (const T*)w->q[pi],
+                                                      (const T*)w->Minv[pi], w->cg, w->partial);
+        cg_pupdate<D, T><<<grid_dofs(), kVT, 0, st_>>>(w->nn, (T*)w->p[pi], (const T*)w->z[pi], w->cg);
+        CUDA_TRY(cudaGetLastError());
+        return FEM_OK;
+    }
+
+    // PCG on M K M x = b (b in w->b) from x = 0 to ||res|| <= tol; the
+    // number of HVPs goes to *iters
+    template <int D, typename T>
+    fem_status pcg_t(const void* ucg, double tol, int64_t* iters) {
+        SolverWork* w = w_;
+        const int pi = pi_;
+        SolverWork::Host* h = w->h;
+        h->cg.tol = tol;
+        h->cg.cg_max = cg_max_;
+        // only tol and cg_max are read before cg_init writes the rest
+        CUDA_TRY(cudaMemcpyAsync(&w->cg->tol, &h->cg.tol, sizeof(double), cudaMemcpyHostToDevice, st_));
+        CUDA_TRY(cudaMemcpyAsync(&w->cg->cg_max, &h->cg.cg_max, sizeof(long long), cudaMemcpyHostToDevice, st_));
+        cg_init<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],
+                                                    (T*)w->z[pi], (T*)w->p[pi], (const T*)w->Minv[pi], w->cg,
+                                                    w->partial);
+        CUDA_TRY(cudaGetLastError());
+        const int B = o_.cg_batch > 0 ? o_.cg_batch : 8;
+        const int64_t max_batches = cg_max_ / B + 3;
+        for (int64_t j = 0; j < max_batches; ++j) {
+            for (int i = 0; i < B; ++i) FEM_TRY((launch_cg_iteration<D, T>(ucg)));
+            CUDA_TRY(cudaMemcpyAsync(&h->done[j & 1], &w->cg->done, sizeof(int), cudaMemcpyDeviceToHost, st_));
+            CUDA_TRY(cudaEventRecord(w->ev[j & 1], st_));
+            if (j >= 1) {
+                CUDA_TRY(cudaEventSynchronize(w->ev[(j - 1) & 1]));
+                if (h->done[(j - 1) & 1]) break;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(&h->cg, w->cg, sizeof(CgState), cudaMemcpyDeviceToHost, st_));
+        FEM_TRY(sync());
+        if (!h->cg.done) return fail(FEM_ERR_CUDA, "PCG ended without a final state");
+        *iters = h->cg.k;
+        return FEM_OK;
+    }
+
+    fem_status pcg(const void* ucg, double tol, int64_t* iters) {
+        if (D_ == 2) return pi_ == 0 ? pcg_t<2, double>(ucg, tol, iters) : pcg_t<2, float>(ucg, tol, iters);
+        return pi_ == 0 ? pcg_t<3, double>(ucg, tol, iters) : pcg_t<3, float>(ucg, tol, iters);
+    }
+
+    // b = -src (src FP64 or the CG dtype)
+    void set_rhs_neg(const void* src, int src_dt) {
+        const int g = grid_dofs();
+        if (pi_ == 0)
+            negate<double, double><<<g, kVT, 0, st_>>>(w_->nd, (const double*)src, (double*)w_->b[0]);
+        else if (src_dt == FEM_F64)
+            negate<double, float><<<g, kVT, 0, st_>>>(w_->nd, (const double*)src, (float*)w_->b[1]);
+        else
+            negate<float, float><<<g, kVT, 0, st_>>>(w_->nd, (const float*)src, (float*)w_->b[1]);
+    }
+
+    int increment(double* u, const double* ubar, double s0, double s1, fem_status* err) {
+#define STEP_TRY(call)             \
+    do {                           \
+        *err = (call);             \
+        if (*err != FEM_OK) return -1; \
+    } while (0)
+        SolverWork* w = w_;
+        const int64_t nn = w->nn, nd = w->nd;
+        const int gn = grid_nodes(), gd = grid_dofs();
+        // 1-2: prescribed increment and linearised predictor
+        if (D_ == 2)
+            predictor_increment<2><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, ubar, s1 - s0, w->du, pi_ ? w->du32 : nullptr);
+        else
+            predictor_increment<3><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, ubar, s1 - s0, w->du, pi_ ? w->du32 : nullptr);
+        const void* ucg = cg_state(u);
+        void* tv = pi_ == 0 ? (void*)w->t : w->q[1];  // predictor rhs in the CG dtype
+        STEP_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, pi_ == 0 ? (const void*)w->du : (const void*)w->du32, tv,
+                              nullptr, FEM_MASK_OUT, st_, nullptr));
+        double r0sq = 0.0;
+        STEP_TRY(dot(tv, dt_, tv, dt_, &r0sq));
+        double r0 = std::sqrt(r0sq);
+        if (!std::isfinite(r0)) return 3;
+        if (r0 > 0.0) {
+            const int rc = build_block_jacobi(ucg, err);
+            if (rc != 0) return rc;
+            set_rhs_neg(tv, dt_);
+            int64_t it = 0;
+            STEP_TRY(pcg(ucg, o_.predictor_rtol * r0, &it));
+            stats_->cg_iters += it;
+            if (D_ == 2) {
+                if (pi_ == 0)
+                    apply_predictor<2, double><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, w->du, (const double*)w->x[0]);
+                else
+                    apply_predictor<2, float><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, w->du, (const float*)w->x[1]);
+            } else {
+                if (pi_ == 0)
+                    apply_predictor<3, double><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, w->du, (const double*)w->x[0]);
+                else
+                    apply_predictor<3, float><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, w->du, (const float*)w->x[1]);
+            }
+        }
+        if (D_ == 2)
+            set_prescribed<2><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, ubar, s1);
+        else
+            set_prescribed<3><<<gn, kVT, 0, st_>>>(nn, m_->node_mask, u, ubar, s1);
+        double psi = 0.0, S = 0.0;
+        STEP_TRY(energy(u, &psi, &S));
+        if (!std::isfinite(psi)) return 3;
+        STEP_TRY(residual(u, w->r));
+        double rsq = 0.0;
+        STEP_TRY(dot(w->r, FEM_F64, w->r, FEM_F64, &rsq));
+        double rn = std::sqrt(rsq);
+        if (!(r0 > 0.0)) r0 = rn;
+        stats_->r0_norm = r0;
+        // 3: Newton loop
+        for (int it = 0; it <= o_.newton_max; ++it) {
+            stats_->r_norm = rn;
+            if (rn <= o_.newton_rtol * r0) return 0;
+            if (it == o_.newton_max) return 6;
+            stats_->newton_iters++;
+            const double eta = std::min(o_.eta_max, std::sqrt(rn / r0));
+            ucg = cg_state(u);
+            const int rc = build_block_jacobi(ucg, err);
+            if (rc != 0) return rc;
+            set_rhs_neg(w->r, FEM_F64);
+            int64_t cgit = 0;
+            STEP_TRY(pcg(ucg, eta * rn, &cgit));
+            stats_->cg_iters += cgit;
+            const void* xd = w->x[pi_];
+            double g = 0.0;
+            STEP_TRY(dot(w->r, FEM_F64, xd, dt_, &g));
+            double alpha = 1.0;
+            bool ok = false;
+            for (int ls = 0; ls <= o_.ls_max; ++ls) {
+                if (pi_ == 0)
+                    trial_point<double><<<gd, kVT, 0, st_>>>(nd, u, alpha, (const double*)xd, w->ut);
+                else
+                    trial_point<float><<<gd, kVT, 0, st_>>>(nd, u, alpha, (const float*)xd, w->ut);
+                double pt = 0.0, St = 0.0;
+                STEP_TRY(energy(w->ut, &pt, &St));
+                if (std::isfinite(pt)) {
+                    if (pt <= psi + o_.armijo_c * alpha * g) {
+                        ok = true;
+                    } else if (std::fabs(pt - psi) <= 16.0 * kEps * S) {
+                        STEP_TRY(residual(w->ut, w->t));
+                        double rtsq = 0.0;
+                        STEP_TRY(dot(w->t, FEM_F64, w->t, FEM_F64, &rtsq));
+                        if (std::sqrt(rtsq) < rn) ok = true;
+                    }
+                }
+                if (ok) {
+                    psi = pt;
+                    S = St;
+                    break;
+                }
+                alpha *= 0.5;
+                stats_->ls_halvings++;
+            }
+            if (!ok) return 7;
+            if (cudaMemcpyAsync(u, w->ut, sizeof(double) * nd, cudaMemcpyDeviceToDevice, st_) != cudaSuccess) {
+                *err = fail(FEM_ERR_CUDA, "cudaMemcpyAsync (accept) failed");
+                return -1;
+            }
+            STEP_TRY(residual(u, w->r));
+            STEP_TRY(dot(w->r, FEM_F64, w->r, FEM_F64, &rsq));
+            rn = std::sqrt(rsq);
+        }
+        return 6;
+#undef STEP_TRY
+    }
+
+    static constexpr double kEps = 2.220446049250313e-16;
+};
+
+fem_status status_of(int rc) {
+    switch (rc) {
+        case 0: return FEM_OK;
+        case 3: return FEM_ERR_INVERTED;
+        case 5: return FEM_ERR_NOT_SPD;
+        case 6: return FEM_ERR_NOT_CONVERGED;
+        case 7: return FEM_ERR_LINESEARCH;
+        default: return FEM_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+fem_status fem_newton_default_opts(fem_newton_opts* o) {
+    if (!o) return fail(FEM_ERR_ARG, "null options");
+    std::memset(o, 0, sizeof *o);
+    o->cg_dtype = FEM_F64;
+    o->precond = FEM_PC_BLOCK_JACOBI;
+    o->newton_rtol = 1e-8;
+    o->newton_max = 50;
+    o->eta_max = 0.1;
+    o->cg_max = 0;
+    o->predictor_rtol = 1e-2;
+    o->armijo_c = 1e-4;
+    o->ls_max = 20;
+    o->max_bisect = 5;
+    o->cg_batch = 8;
+    return FEM_OK;
+}
+
+fem_status fem_newton_step(fem_mesh* m, double* u, const double* ubar, double s_prev, double s,
+                           const fem_newton_opts* opts, fem_newton_stats* stats, void* stream) {
+    if (!m || !u || !ubar || !stats) return fail(FEM_ERR_ARG, "null mesh, u, ubar or stats");
+    fem_newton_opts o;
+    if (opts)
+        o = *opts;
+    else
+        fem_newton_default_opts(&o);
+    if (o.cg_dtype != FEM_F64 && o.cg_dtype != FEM_F32) return fail(FEM_ERR_ARG, "cg_dtype must be FEM_F64 or FEM_F32");
+    if (o.cg_dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "cg_dtype FEM_F32 needs a mesh created with FEM_PREC_MIXED");
+    if (o.precond != FEM_PC_BLOCK_JACOBI) return fail(FEM_ERR_ARG, "unknown preconditioner");
+    if (o.newton_max < 0 || o.ls_max < 0 || o.max_bisect < 0 || o.cg_max < 0)
+        return fail(FEM_ERR_ARG, "negative iteration limit");
+    if (!(s >= s_prev) || !std::isfinite(s) || !std::isfinite(s_prev)) return fail(FEM_ERR_ARG, "need finite s >= s_prev");
+    std::memset(stats, 0, sizeof *stats);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FEM_TRY(ensure_work(m, o.cg_dtype));
+    SolverWork* w = m->solver;
+    // keep the caller's status word: trial states of the line search may
+    // raise the inverted flag, which the step handles itself
+    CUDA_TRY(cudaMemcpyAsync(&w->h->status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const int status_in = w->h->status;
+    Stepper stepper(m, o, stats, st);
+    fem_status err = FEM_OK;
+    const int rc = stepper.step_rec(u, ubar, s_prev, s, 0, &err);
+    w->h->status = status_in;
+    CUDA_TRY(cudaMemcpyAsync(m->status, &w->h->status, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (err != FEM_OK) {
+        stats->status = err;
+        return err;
+    }
+    const fem_status fs = status_of(rc);
+    stats->status = fs;
+    if (rc != 0)
+        return fail(fs, "fem_newton_step: " + std::string(rc == 3   ? "inverted elements"
+                                                                   : rc == 5 ? "a nodal block is not SPD"
+                                                                   : rc == 6 ? "Newton iteration cap reached"
+                                                                             : "line search failed") +
+                                       " after all bisections");
+    return FEM_OK;
+}
+
+}  // extern "C"

@@ -176,6 +176,30 @@ class Mesh:
                                       _stream(stream)))
         return gm, gl
 
+    def newton_step(self, u, ubar, s_prev, s, cg_dtype=torch.float64, check=True, stream=None,
+                    **opts):
+        """One Newton-CG load step from s_prev to s (fem_newton_step); u (FP64,
+        on the device) is updated in place.  ``cg_dtype`` float32 runs the PCG
+        in FP32 with FP64 dots; keyword ``opts`` override fem_newton_opts
+        fields.  Returns the step statistics as a dict; with ``check`` a
+        failed step raises FemError."""
+        if u.dtype != torch.float64 or ubar.dtype != torch.float64:
+            raise TypeError("u and ubar must be float64 (the master state is FP64)")
+        self._check_vec(u, ubar)
+        o = L.NewtonOpts()
+        L.check(L.lib().fem_newton_default_opts(C.byref(o)))
+        o.cg_dtype = L.FEM_F64 if cg_dtype == torch.float64 else L.FEM_F32
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        st = L.NewtonStats()
+        rc = L.lib().fem_newton_step(self._h, _ptr(u), _ptr(ubar), float(s_prev), float(s),
+                                     C.byref(o), C.byref(st), _stream(stream))
+        if check:
+            L.check(rc)
+        return st.as_dict()
+
     def sync_status(self, stream=None) -> int:
         f = C.c_int32(0)
         L.check(L.lib().fem_sync_status(self._h, _stream(stream), C.byref(f)))

@@ -1,0 +1,147 @@
+"""GPU Newton-CG load steps (fem_newton_step) against the FP64 oracle.
+
+The driver and the oracle run the same algorithm (predictor, Eisenstat-Walker
+PCG with block Jacobi, Armijo backtracking with the roundoff guard,
+bisection), so on the same problem they converge to the same displacements:
+the bar is 1e-6 relative on u for both CG precisions.  The uniaxial bar has a
+homogeneous exact solution (a scalar equation for the lateral stretch), which
+pins the GPU solve independently of the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+from scipy.optimize import brentq
+
+import oracle
+from paper_2602_12365_b300 import meshgen as mg
+from paper_2602_12365_b300._lib import FemError
+from paper_2602_12365_b300.fem import Mesh
+
+pytestmark = pytest.mark.gpu
+
+MU, LAM = 1.0, 10.0
+
+
+def _gpu_path(m, steps, cg_dtype, precision="mixed", **opts):
+    gm = Mesh.from_fixture(m, precision=precision)
+    u = torch.zeros(m.n_nodes * m.dim, dtype=torch.float64, device="cuda")
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    stats, s_prev = [], 0.0
+    for s in steps:
+        stats.append(gm.newton_step(u, ubar, s_prev, s, cg_dtype=cg_dtype, **opts))
+        s_prev = s
+    assert gm.sync_status() == 0
+    return u.cpu().numpy(), stats, gm
+
+
+def _oracle_path(m, steps):
+    om = oracle.OracleMesh.from_mesh(m)
+    u = np.zeros(m.n_nodes * m.dim)
+    stats, s_prev = [], 0.0
+    for s in steps:
+        st = om.load_step(m.ubar, s_prev, s, u)
+        assert st.status == 0
+        stats.append(st)
+        s_prev = s
+    return u, stats
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_plane_strain_load_path_fp64_matches_oracle():
+    # 32 x 32 P1 square, left edge clamped, right edge pulled to 0.1 in 10 steps
+    m = mg.workload_tri(32)
+    steps = [k / 10 for k in range(1, 11)]
+    ug, sg, _ = _gpu_path(m, steps, torch.float64, precision="fp64")
+    uo, so = _oracle_path(m, steps)
+    assert _rel(ug, uo) <= 1e-6
+    for a, b in zip(sg, so):
+        assert a["status"] == 0
+        assert a["r_norm"] <= 1e-8 * a["r0_norm"]
+        assert abs(a["newton_iters"] - b.newton_iters) <= 1
+        assert abs(a["cg_iters"] - b.cg_iters) <= max(3, 0.05 * b.cg_iters)
+
+
+@pytest.mark.parametrize("cg_dtype", [torch.float64, torch.float32])
+def test_compressed_tet_block_matches_oracle(cg_dtype):
+    # jittered Kuhn tets, base clamped, top compressed (4 % in 4 steps)
+    m = mg.workload_tet(6, seed=1)
+    steps = [0.05 * k for k in range(1, 5)]
+    ug, sg, _ = _gpu_path(m, steps, cg_dtype)
+    uo, _ = _oracle_path(m, steps)
+    assert _rel(ug, uo) <= 1e-6
+    for a in sg:
+        assert a["status"] == 0 and a["r_norm"] <= 1e-8 * a["r0_norm"]
+
+
+def test_random_moduli_mixed_matches_oracle():
+    m = mg.workload_tet(5, seed=2, random_moduli=7)
+    steps = [0.05, 0.1]
+    ug, _, _ = _gpu_path(m, steps, torch.float32)
+    uo, _ = _oracle_path(m, steps)
+    assert _rel(ug, uo) <= 1e-6
+
+
+def _lateral_stretch(dim, delta):
+    if dim == 2:
+        f = lambda b: MU * (b - 1 / b) + LAM * np.log((1 + delta) * b) / b
+    else:
+        f = lambda b: MU * (b - 1 / b) + LAM * np.log(b * b * (1 + delta)) / b
+    return brentq(f, 0.3, 2.0, xtol=1e-15, rtol=1e-15)
+
+
+@pytest.mark.parametrize("kind", ["tri", "tet"])
+@pytest.mark.parametrize("cg_dtype", [torch.float64, torch.float32])
+def test_uniaxial_bar_homogeneous_solution(kind, cg_dtype):
+    delta = 0.3
+    m = mg.bc_uniaxial_bar(mg.tri_mesh(4) if kind == "tri" else mg.tet_mesh(2), delta)
+    ug, sg, _ = _gpu_path(m, (0.5, 1.0), cg_dtype)
+    b = _lateral_stretch(m.dim, delta)
+    X = m.coords
+    if m.dim == 2:
+        exact = np.stack([delta * X[:, 0], (b - 1) * X[:, 1]], axis=1)
+    else:
+        exact = np.stack([(b - 1) * X[:, 0], (b - 1) * X[:, 1], delta * X[:, 2]], axis=1)
+    assert _rel(ug, exact.ravel()) <= 1e-8
+
+
+def test_bitwise_reproducible_mixed():
+    m = mg.workload_tet(6, seed=3)
+    a, sa, _ = _gpu_path(m, (0.05,), torch.float32)
+    b, sb, _ = _gpu_path(m, (0.05,), torch.float32)
+    assert np.array_equal(a, b)
+    assert sa == sb
+
+
+def test_result_independent_of_cg_batch():
+    m = mg.workload_tet(5, seed=4)
+    a, sa, _ = _gpu_path(m, (0.05,), torch.float32, cg_batch=1)
+    b, sb, _ = _gpu_path(m, (0.05,), torch.float32, cg_batch=13)
+    assert np.array_equal(a, b)
+    assert sa == sb
+
+
+def test_zero_increment_at_rest_does_nothing():
+    m = mg.workload_tri(8)
+    gm = Mesh.from_fixture(m, precision="fp64")
+    u = torch.zeros(m.n_nodes * 2, dtype=torch.float64, device="cuda")
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    st = gm.newton_step(u, ubar, 0.0, 0.0)
+    assert st["status"] == 0 and st["newton_iters"] == 0 and st["cg_iters"] == 0
+    assert st["r_norm"] == 0.0
+    assert not torch.any(u)
+
+
+def test_argument_errors():
+    m = mg.workload_tri(4)
+    gm = Mesh.from_fixture(m, precision="fp64")
+    u = torch.zeros(m.n_nodes * 2, dtype=torch.float64, device="cuda")
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    with pytest.raises(FemError, match="FEM_PREC_MIXED"):
+        gm.newton_step(u, ubar, 0.0, 1.0, cg_dtype=torch.float32)
+    with pytest.raises(FemError, match="s >= s_prev"):
+        gm.newton_step(u, ubar, 1.0, 0.5)
+    with pytest.raises(TypeError):
+        gm.newton_step(u.float(), ubar, 0.0, 1.0)
