@@ -45,7 +45,8 @@
 namespace {
 
 constexpr int kVT = 256;          // threads of the vector kernels
-constexpr int kMaxRedBlocks = 1184;  // 8 per SM on 148 SMs
+constexpr int kMaxRedBlocks = 1184;  // partial-sum slots (8 blocks per SM on 148 SMs)
+constexpr int kVecBlocks = 592;      // grid of the vector kernels: 4 blocks per SM
 
 // device-resident scalars of one PCG solve
 struct CgState {
@@ -66,6 +67,58 @@ struct DotState {
     unsigned counter;
     int pad;
 };
+
+// ---------------------------------------------------------------------------
+// Dot-product accumulators.  FP64 vectors add in double.  FP32 vectors keep
+// an unevaluated float pair hi + lo: each product a*b is split exactly into
+// p + e by an FMA (e = fma(a, b, -p)) and added with Knuth's TwoSum, so the
+// pair carries the sum to about 2^-44 relative; it is widened to double once
+// per warp.  On this GPU FP64 instructions issue at a small fraction of the
+// FP32 rate, and these sums run in every CG iteration.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi = 0.f, lo = 0.f;
+};
+
+__device__ __forceinline__ void ff_add(FF& s, float x) {
+    const float t = s.hi + x;
+    const float bp = t - s.hi;
+    s.lo += (s.hi - (t - bp)) + (x - bp);
+    s.hi = t;
+}
+__device__ __forceinline__ void acc_prod(FF& s, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    ff_add(s, p);
+    s.lo += e;
+}
+__device__ __forceinline__ void acc_prod(double& s, double a, double b) { s = fma(a, b, s); }
+
+template <typename T>
+struct AccT {
+    using type = double;
+};
+template <>
+struct AccT<float> {
+    using type = FF;
+};
+
+// warp butterfly on the accumulator, widened to double (all lanes)
+__device__ __forceinline__ double warp_total(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_total(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        ff_add(v, oh);
+        v.lo += ol;
+    }
+    return (double)v.hi + (double)v.lo;
+}
 
 // ---------------------------------------------------------------------------
 // fixed-order block reduction of NV doubles; the total lands in thread 0
@@ -90,11 +143,23 @@ __device__ __forceinline__ void block_total(double (&v)[NV], double* sh /* [kVT/
 
 // Each block stores its partial sums; the last block to arrive adds the
 // partials in block order and returns true (its thread 0 holds the totals).
-template <int NV>
-__device__ __forceinline__ bool grid_total(double (&v)[NV], double* partial, unsigned* counter) {
+// A: double, or FF (FP32 pairs, widened per warp).
+template <int NV, typename A>
+__device__ __forceinline__ bool grid_total(A (&a)[NV], double (&out)[NV], double* partial, unsigned* counter) {
     __shared__ double sh[kVT / 32 * NV];
     __shared__ int last;
-    block_total<NV>(v, sh);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_total(a[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kVT / 32; ++w)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] += sh[w * NV + k];
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) partial[blockIdx.x * NV + k] = v[k];
@@ -113,7 +178,7 @@ __device__ __forceinline__ bool grid_total(double (&v)[NV], double* partial, uns
     block_total<NV>(t, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = t[k];
+        for (int k = 0; k < NV; ++k) out[k] = t[k];
         *counter = 0u;
     }
     return true;
@@ -138,7 +203,7 @@ __device__ __forceinline__ void apply_block(const T* Minv, int64_t n, const T (&
 template <int D, typename T>
 __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* res, T* z, T* p,
                                                const T* Minv, CgState* st, double* partial) {
-    double v[2] = {0.0, 0.0};
+    typename AccT<T>::type v[2] = {};
     for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
         T r[3] = {0, 0, 0}, zz[3];
 #pragma unroll
@@ -150,16 +215,28 @@ __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* 
             res[n * D + c] = r[c];
             z[n * D + c] = zz[c];
             p[n * D + c] = zz[c];
-            v[0] += (double)r[c] * (double)r[c];
-            v[1] += (double)r[c] * (double)zz[c];
+            acc_prod(v[0], r[c], r[c]);
+            acc_prod(v[1], r[c], zz[c]);
         }
     }
-    if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
-        st->rr = v[0];
-        st->rz = v[1];
+    double tot[2];
+    if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->rz = tot[1];
         st->k = 0;
-        st->done = (sqrt(v[0]) <= st->tol) ? 1 : 0;
+        st->done = (sqrt(tot[0]) <= st->tol) ? 1 : 0;
     }
+}
+
+// pq = p . q for the step length (a separate pass: p and q are still in L2)
+template <int D, typename T>
+__global__ void __launch_bounds__(kVT) cg_pq(int64_t nn, const T* p, const T* q, CgState* st, double* partial) {
+    if (st->done) return;  // uniform: only the last block of a kernel writes done
+    typename AccT<T>::type v[1] = {};
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < nn * D; i += (int64_t)gridDim.x * kVT)
+        acc_prod(v[0], p[i], q[i]);
+    double tot[1];
+    if (grid_total<1>(v, tot, partial, &st->counter) && threadIdx.x == 0) st->pq = tot[0];
 }
 
 // alpha = rz / pq; x += alpha p; res -= alpha q; z = Minv res; new rz, rr;
@@ -167,17 +244,18 @@ __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* 
 template <int D, typename T>
 __global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z, const T* p, const T* q,
                                                  const T* Minv, CgState* st, double* partial) {
-    if (st->done) return;  // uniform: only the last block of a kernel writes done
+    if (st->done) return;
     const double pq = st->pq, rz = st->rz;
     const int k = st->k;
-    double v[2] = {0.0, 0.0};
+    typename AccT<T>::type v[2] = {};
+    double tot[2];
     if (!(pq > 0.0)) {
         // non-positive curvature: stop; at the first iteration take d = P r
         if (k == 0)
             for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT)
 #pragma unroll
                 for (int c = 0; c < D; ++c) x[n * D + c] = z[n * D + c];
-        if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
+        if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
             st->k = k + 1;
             st->done = 2;
         }
@@ -196,19 +274,19 @@ __global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z,
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             z[n * D + c] = zz[c];
-            v[0] += (double)r[c] * (double)r[c];
-            v[1] += (double)r[c] * (double)zz[c];
+            acc_prod(v[0], r[c], r[c]);
+            acc_prod(v[1], r[c], zz[c]);
         }
     }
-    if (grid_total<2>(v, partial, &st->counter) && threadIdx.x == 0) {
+    if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
         const int k1 = k + 1;
         st->k = k1;
-        st->rr = v[0];
-        if (sqrt(v[0]) <= st->tol) {
+        st->rr = tot[0];
+        if (sqrt(tot[0]) <= st->tol) {
             st->done = 1;
         } else {
-            st->beta = v[1] / rz;
-            st->rz = v[1];
+            st->beta = tot[1] / rz;
+            st->rz = tot[1];
             if (k1 >= st->cg_max) st->done = 3;
         }
     }
@@ -228,8 +306,9 @@ __global__ void __launch_bounds__(kVT) dot_kernel(int64_t n, const TA* a, const 
                                                   double* partial) {
     double v[1] = {0.0};
     for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
-        v[0] += (double)a[i] * (double)b[i];
-    if (grid_total<1>(v, partial, &ds->counter) && threadIdx.x == 0) ds->value = v[0];
+        v[0] = fma((double)a[i], (double)b[i], v[0]);
+    double tot[1];
+    if (grid_total<1>(v, tot, partial, &ds->counter) && threadIdx.x == 0) ds->value = tot[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -341,7 +420,7 @@ __global__ void block_jacobi_inverse(int64_t nn, const T* Db, T* Minv, int* bad)
 
 int grid_for(int64_t work) {
     const int64_t g = (work + kVT - 1) / kVT;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, kVecBlocks));
 }
 
 fem_status fail(fem_status s, const std::string& msg) { return femi::set_error(s, msg); }
@@ -595,8 +674,9 @@ private:
     fem_status launch_cg_iteration(const void* ucg) {
         SolverWork* w = w_;
         const int pi = pi_;
-        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->p[pi], w->q[pi], &w->cg->pq, FEM_MASK_IN | FEM_MASK_OUT,
+        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->p[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
                              st_, &w->cg->done));
+        cg_pq<D, T><<<grid_dofs(), kVT, 0, st_>>>(w->nn, (const T*)w->p[pi], (const T*)w->q[pi], w->cg, w->partial);
         cg_update<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
                                                       (const T*)w->p[pi], (const T*)w->q[pi],
                                                       (const T*)w->Minv[pi], w->cg, w->partial);

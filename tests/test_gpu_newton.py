@@ -104,7 +104,10 @@ def test_uniaxial_bar_homogeneous_solution(kind, cg_dtype):
         exact = np.stack([delta * X[:, 0], (b - 1) * X[:, 1]], axis=1)
     else:
         exact = np.stack([(b - 1) * X[:, 0], (b - 1) * X[:, 1], delta * X[:, 2]], axis=1)
-    assert _rel(ug, exact.ravel()) <= 1e-8
+    # the stop test bounds the residual (1e-8 r0), not u: the error in u is
+    # that times the conditioning, and an FP32 CG leaves a different final
+    # residual below the threshold than an FP64 one
+    assert _rel(ug, exact.ravel()) <= (1e-8 if cg_dtype == torch.float64 else 1e-7)
 
 
 def test_bitwise_reproducible_mixed():
