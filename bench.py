@@ -13,6 +13,10 @@ L2 (126 MB) is flushed before every timed step by writing a 256 MB buffer and
 then reading another 256 MB one (so the flush's dirty lines are written back
 before the timed kernels start); each step is timed with CUDA events on the
 stream the kernels run on.
+The line also carries the Newton-CG measurement ("newton"): seconds per load
+step to relative residual 1e-8 on the 64^3 random-moduli tet mesh, FP64
+against mixed precision (FP32 CG with FP64 dots, FP64 residual and energy),
+both with block-Jacobi PCG.
 `--impl reference` times the FP64 CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
@@ -47,6 +51,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="cells per side")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--newton-steps", type=int, default=2,
+                    help="load steps of the Newton-CG measurement per arm (0 = skip)")
     return ap.parse_args()
 
 
@@ -231,6 +237,51 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+NEWTON_WORKLOAD = ("tet64 random moduli: 64^3 Kuhn tets (jitter seed 101), per-element mu "
+                   "lognormal(0, 0.5) (seed 101), lambda = 10 mu; base clamped, top compressed "
+                   "20 % in 20 load steps")
+
+
+def newton_arms(n, n_steps, dev):
+    """Seconds per Newton-CG load step (relative residual 1e-8), FP64 vs mixed
+    precision, block-Jacobi PCG, over the first n_steps of the 20-step path."""
+    import torch
+    from paper_2602_12365_b300 import meshgen as mg
+    from paper_2602_12365_b300.fem import Mesh
+    m = mg.workload_tet(n, seed=101, random_moduli=101)
+    gm = Mesh.from_fixture(m, precision="mixed")
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out, finals = {}, {}
+    for arm, dt in (("fp64_block_jacobi", torch.float64), ("mixed_block_jacobi", torch.float32)):
+        u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device=dev)
+        times, newton, cg = [], [], []
+        s_prev = 0.0
+        for k in range(1, n_steps + 1):
+            s = k / 20
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=dt)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) * 1e-3)
+            newton.append(st["newton_iters"])
+            cg.append(st["cg_iters"])
+            s_prev = s
+        finals[arm] = u
+        out[arm] = {"s_per_load_step": statistics.median(times), "s_each": times,
+                    "newton_iters": newton, "cg_iters": cg}
+    ref = finals["fp64_block_jacobi"]
+    for arm, u in finals.items():
+        out[arm]["u_rel_diff_vs_fp64"] = float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref))
+    return {"workload": NEWTON_WORKLOAD, "metric": "Newton-CG s/load step at relative residual 1e-8",
+            "load_steps": list(range(1, n_steps + 1)), "arms": out,
+            "speedup_mixed_vs_fp64": out["fp64_block_jacobi"]["s_per_load_step"]
+            / out["mixed_block_jacobi"]["s_per_load_step"]}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_init(args)
@@ -354,6 +405,8 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
+    if args.newton_steps > 0:
+        line["newton"] = newton_arms(args.n, args.newton_steps, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, t = cpu_oracle_rate(m, u, v)
         line["cpu_baseline"] = {"value": rate, "unit": "GElem/s", "cores": 1, "kind": "oracle",

@@ -305,6 +305,23 @@ fem_status fem_newton_default_opts(fem_newton_opts* opts);
 fem_status fem_newton_step(fem_mesh* mesh, double* u, const double* ubar, double s_prev, double s,
                            const fem_newton_opts* opts, fem_newton_stats* stats, void* stream);
 
+/*
+ * fem_tangent_solve -- the linear solve inside a Newton step, exposed for
+ * adjoint (design-sensitivity) solves: block-Jacobi PCG on
+ * M K(u) M x = M b from x = 0 until ||M b - M K M x|| <= rtol ||M b||, with
+ * the same kernels, precisions and FP64 dot products as fem_newton_step.
+ *   u  DEVICE double[n_nodes * dim], the linearisation state.
+ *   b  DEVICE double[n_nodes * dim]; prescribed components are ignored.
+ *   x  DEVICE double[n_nodes * dim] (out); prescribed components are 0.
+ *   cg_max 0 = 10 * n_dofs; *iters (HOST, may be NULL) receives the HVP
+ *   count.  Synchronises `stream`; allocates the solver workspace on first
+ *   use like fem_newton_step.
+ * Returns FEM_OK, FEM_ERR_NEG_CURVATURE (x = last iterate),
+ * FEM_ERR_NOT_CONVERGED, FEM_ERR_NOT_SPD, FEM_ERR_ARG or FEM_ERR_CUDA.
+ */
+fem_status fem_tangent_solve(fem_mesh* mesh, int cg_dtype, const double* u, const double* b, double* x,
+                             double rtol, int64_t cg_max, int64_t* iters, void* stream);
+
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */
 fem_status fem_sync_status(fem_mesh* mesh, void* stream, int32_t* flags);

@@ -94,6 +94,7 @@ def lib():
             "fem_param_vjp": [P, i32, P, P, P, P, P],
             "fem_sync_status": [P, P, C.POINTER(i32)],
             "fem_newton_default_opts": [C.POINTER(NewtonOpts)],
+            "fem_tangent_solve": [P, i32, P, P, P, C.c_double, C.c_int64, C.POINTER(C.c_int64), P],
             "fem_newton_step": [P, P, P, C.c_double, C.c_double, C.POINTER(NewtonOpts),
                                 C.POINTER(NewtonStats), P],
         }
@@ -113,4 +114,5 @@ def check(status: int):
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_plan_partition",
             "fem_energy", "fem_energy_static", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
-            "fem_sync_status", "fem_newton_default_opts", "fem_newton_step", "fem_last_error"]
+            "fem_sync_status", "fem_newton_default_opts", "fem_newton_step", "fem_tangent_solve",
+            "fem_last_error"]

@@ -340,6 +340,22 @@ __global__ void negate(int64_t n, const TS* a, TD* b) {
         b[i] = -(TD)a[i];
 }
 
+// dst = src with prescribed components zeroed (FP64 -> the CG dtype)
+template <int D, typename TD>
+__global__ void masked_copy(int64_t nn, const uint8_t* mask, const double* src, TD* dst) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        const uint8_t m = mask[n];
+#pragma unroll
+        for (int c = 0; c < D; ++c) dst[n * D + c] = ((m >> c) & 1) ? TD(0) : (TD)src[n * D + c];
+    }
+}
+
+template <typename TS>
+__global__ void widen(int64_t n, const TS* a, double* b) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        b[i] = (double)a[i];
+}
+
 // u += du on prescribed DOFs, u += x elsewhere
 template <int D, typename T>
 __global__ void apply_predictor(int64_t nn, const uint8_t* mask, double* u, const double* du, const T* x) {
@@ -583,6 +599,42 @@ public:
             if (rc == 0 && *err == FEM_OK) rc = step_rec(u, ubar, sm, s1, depth + 1, err);
         }
         return rc;
+    }
+
+    // x = PCG solution of M K(u) M x = M b from 0 to ||res|| <= rtol ||M b||
+    // (b, x FP64); returns 0, 2 (non-positive curvature) or 3 (iteration cap)
+    int tangent_solve(const double* u, const double* b, double* x, double rtol, int64_t* iters, fem_status* err) {
+        const void* ucg = cg_state(u);
+        const int rc = build_block_jacobi(ucg, err);
+        if (*err != FEM_OK) return -1;
+        if (rc != 0) return 5;
+        const int gn = grid_nodes(), gd = grid_dofs();
+        if (D_ == 2) {
+            if (pi_ == 0)
+                masked_copy<2, double><<<gn, kVT, 0, st_>>>(w_->nn, m_->node_mask, b, (double*)w_->b[0]);
+            else
+                masked_copy<2, float><<<gn, kVT, 0, st_>>>(w_->nn, m_->node_mask, b, (float*)w_->b[1]);
+        } else {
+            if (pi_ == 0)
+                masked_copy<3, double><<<gn, kVT, 0, st_>>>(w_->nn, m_->node_mask, b, (double*)w_->b[0]);
+            else
+                masked_copy<3, float><<<gn, kVT, 0, st_>>>(w_->nn, m_->node_mask, b, (float*)w_->b[1]);
+        }
+        double bb = 0.0;
+        *err = dot(w_->b[pi_], dt_, w_->b[pi_], dt_, &bb);
+        if (*err != FEM_OK) return -1;
+        *err = pcg(ucg, rtol * std::sqrt(bb), iters);
+        if (*err != FEM_OK) return -1;
+        if (pi_ == 0)
+            widen<double><<<gd, kVT, 0, st_>>>(w_->nd, (const double*)w_->x[0], x);
+        else
+            widen<float><<<gd, kVT, 0, st_>>>(w_->nd, (const float*)w_->x[1], x);
+        if (cudaStreamSynchronize(st_) != cudaSuccess) {
+            *err = fail(FEM_ERR_CUDA, "cudaStreamSynchronize failed");
+            return -1;
+        }
+        const int done = w_->h->cg.done;
+        return done == 1 ? 0 : done;
     }
 
 private:
@@ -923,6 +975,32 @@ fem_status fem_newton_step(fem_mesh* m, double* u, const double* ubar, double s_
                                                                    : rc == 6 ? "Newton iteration cap reached"
                                                                              : "line search failed") +
                                        " after all bisections");
+    return FEM_OK;
+}
+
+fem_status fem_tangent_solve(fem_mesh* m, int cg_dtype, const double* u, const double* b, double* x,
+                             double rtol, int64_t cg_max, int64_t* iters, void* stream) {
+    if (!m || !u || !b || !x) return fail(FEM_ERR_ARG, "null mesh, u, b or x");
+    if (cg_dtype != FEM_F64 && cg_dtype != FEM_F32) return fail(FEM_ERR_ARG, "cg_dtype must be FEM_F64 or FEM_F32");
+    if (cg_dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "cg_dtype FEM_F32 needs a mesh created with FEM_PREC_MIXED");
+    if (!(rtol > 0.0) || cg_max < 0) return fail(FEM_ERR_ARG, "need rtol > 0 and cg_max >= 0");
+    fem_newton_opts o;
+    fem_newton_default_opts(&o);
+    o.cg_dtype = cg_dtype;
+    o.cg_max = cg_max;
+    fem_newton_stats stats{};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FEM_TRY(ensure_work(m, cg_dtype));
+    Stepper stepper(m, o, &stats, st);
+    fem_status err = FEM_OK;
+    int64_t it = 0;
+    const int rc = stepper.tangent_solve(u, b, x, rtol, &it, &err);
+    if (iters) *iters = it;
+    if (err != FEM_OK) return err;
+    if (rc == 5) return fail(FEM_ERR_NOT_SPD, "fem_tangent_solve: a nodal diagonal block is not SPD");
+    if (rc == 2) return fail(FEM_ERR_NEG_CURVATURE, "fem_tangent_solve: p^T K p <= 0 (K is not positive definite)");
+    if (rc == 3) return fail(FEM_ERR_NOT_CONVERGED, "fem_tangent_solve: iteration cap reached");
     return FEM_OK;
 }
 

@@ -114,6 +114,13 @@ class Mesh:
         except Exception:
             pass
 
+    def dirichlet_mask(self, device=None) -> torch.Tensor:
+        """Boolean per-DOF mask of the prescribed components (all False
+        without Dirichlet data)."""
+        if self.mask is None:
+            return torch.zeros(self.n_nodes * self.dim, dtype=torch.bool, device=device or "cuda")
+        return self.mask if device is None else self.mask.to(device)
+
     @property
     def n_dofs(self):
         return self.n_nodes * self.dim
@@ -199,6 +206,19 @@ class Mesh:
         if check:
             L.check(rc)
         return st.as_dict()
+
+    def tangent_solve(self, u, b, rtol=1e-8, cg_dtype=torch.float64, cg_max=0, stream=None):
+        """x with M K(u) M x = M b (block-Jacobi PCG, fem_tangent_solve);
+        returns (x, iterations)."""
+        if u.dtype != torch.float64 or b.dtype != torch.float64:
+            raise TypeError("u and b must be float64")
+        self._check_vec(u, b)
+        x = torch.empty_like(u)
+        it = C.c_int64(0)
+        L.check(L.lib().fem_tangent_solve(self._h, L.FEM_F64 if cg_dtype == torch.float64 else L.FEM_F32,
+                                          _ptr(u), _ptr(b), _ptr(x), float(rtol), int(cg_max),
+                                          C.byref(it), _stream(stream)))
+        return x, it.value
 
     def sync_status(self, stream=None) -> int:
         f = C.c_int32(0)
