@@ -69,6 +69,12 @@ def lib():
         L.ora_load_step.argtypes = mesh + [P, P, dbl, dbl, P, P, P]
         L.ora_mlp_forward.argtypes = [i32] * 5 + [P] * 8
         L.ora_mlp_backward.argtypes = [i32] * 5 + [P] * 15
+        L.ora_node_graph.restype = i64
+        L.ora_node_graph.argtypes = [i64, i64, i32, P, P, P, i64]
+        L.ora_lp_features.argtypes = [i32, i64, i64, P, P, P, P, P, P]
+        L.ora_lp_blocks.restype = i32
+        L.ora_lp_blocks.argtypes = [i64, P, P, P, P]
+        L.ora_lp_blocks_backward.argtypes = [i64, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -218,3 +224,52 @@ def mlp_backward(x, W1, b1, W2, b2, W3, b3, gy):
     lib().ora_mlp_backward(n, d_in, h1, h2, d_out, _p(x), *[_p(a) for a in Ws], _p(gy),
                            *[_p(g) for g in grads], _p(gx))
     return grads, gx
+
+
+# ----------------------------------------------------------------------------
+# learned block preconditioner (3D): node graph, features, SPD blocks
+# ----------------------------------------------------------------------------
+LP_FEATURES = 36
+
+
+def node_graph(n_nodes, conn):
+    """CSR (ptr, idx) of the distinct nodes sharing an element with each node."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    ne, n_en = conn.shape
+    ptr = np.zeros(n_nodes + 1, np.int64)
+    m = lib().ora_node_graph(n_nodes, ne, n_en, _p(conn), _p(ptr), None, 0)
+    idx = np.zeros(max(m, 1), np.int32)
+    lib().ora_node_graph(n_nodes, ne, n_en, _p(conn), _p(ptr), _p(idx), m)
+    return ptr, idx[:m]
+
+
+def lp_features(elem_type, conn, mu, lam, mask, D):
+    """36 features per node from the diagonal blocks D [n_nodes, 3, 3]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    D = _f64(D).reshape(-1, 9)
+    nn = D.shape[0]
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    F = np.zeros((nn, LP_FEATURES))
+    lib().ora_lp_features(int(elem_type), nn, conn.shape[0], _p(conn), _p(_f64(mu)), _p(_f64(lam)),
+                          None if mk is None else _p(mk), _p(D), _p(F))
+    return F
+
+
+def lp_blocks(D, mask, o):
+    """M_i = F A A^T F^T / s_i (see oracle.c); returns (M [n, 3, 3], ok)."""
+    D = _f64(D).reshape(-1, 9)
+    o = _f64(o).reshape(-1, 6)
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    M = np.zeros((D.shape[0], 9))
+    ok = lib().ora_lp_blocks(D.shape[0], _p(D), None if mk is None else _p(mk), _p(o), _p(M))
+    return M.reshape(-1, 3, 3), bool(ok)
+
+
+def lp_blocks_backward(D, mask, o, gM):
+    D = _f64(D).reshape(-1, 9)
+    o = _f64(o).reshape(-1, 6)
+    gM = _f64(gM).reshape(-1, 9)
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    go = np.zeros((D.shape[0], 6))
+    lib().ora_lp_blocks_backward(D.shape[0], _p(D), None if mk is None else _p(mk), _p(o), _p(gM), _p(go))
+    return go

@@ -746,3 +746,210 @@ void ora_mlp_backward(int n, int d_in, int h1, int h2, int d_out, const double* 
     }
     free(buf);
 }
+
+/* ------------------------------------------------------------------------ */
+/* learned block preconditioner: node graph, features, SPD blocks (3D)      */
+/*                                                                          */
+/* The network replaces block Jacobi M_i = D_i^-1 by a learned correction:  */
+/* with s_i = tr(D_i)/3, Dh = D_i/s_i = C C^T (Cholesky) and F = C^-T,       */
+/*     M_i = F A A^T F^T / s_i,                                             */
+/* A lower-triangular from the 6 outputs o: A_cc = softplus(o) + 1e-4 on the */
+/* diagonal (o0, o2, o5), A_10 = o1, A_20 = o3, A_21 = o4.  A = I gives      */
+/* block Jacobi exactly.  Prescribed components get identity rows/columns.  */
+/* ------------------------------------------------------------------------ */
+static int cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int64_t ora_node_graph(int64_t nn, int64_t ne, int n_en, const int32_t* conn, int64_t* ptr,
+                       int32_t* idx, int64_t cap) {
+    /* every (a, b) pair of an element, a != b, then sort and drop repeats */
+    int64_t* cnt = (int64_t*)calloc((size_t)nn + 1, sizeof(int64_t));
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < n_en; ++a) cnt[conn[e * n_en + a] + 1] += n_en - 1;
+    for (int64_t i = 0; i < nn; ++i) cnt[i + 1] += cnt[i];
+    int32_t* all = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[nn] > 0 ? cnt[nn] : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nn);
+    for (int64_t i = 0; i < nn; ++i) fill[i] = cnt[i];
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < n_en; ++a)
+            for (int b = 0; b < n_en; ++b)
+                if (b != a) {
+                    int32_t na = conn[e * n_en + a];
+                    all[fill[na]++] = conn[e * n_en + b];
+                }
+    int64_t k = 0;
+    ptr[0] = 0;
+    for (int64_t i = 0; i < nn; ++i) {
+        int64_t n0 = cnt[i], n1 = cnt[i + 1];
+        qsort(all + n0, (size_t)(n1 - n0), sizeof(int32_t), cmp_i32);
+        for (int64_t j = n0; j < n1; ++j)
+            if (j == n0 || all[j] != all[j - 1]) {
+                if (idx && k < cap) idx[k] = all[j];
+                ++k;
+            }
+        ptr[i + 1] = k;
+    }
+    free(all);
+    free(fill);
+    free(cnt);
+    return k;
+}
+
+void ora_lp_features(int etype, int64_t nn, int64_t ne, const int32_t* conn, const double* mu,
+                     const double* lam, const uint8_t* mask, const double* D, double* Fo) {
+    const int ne_n = ora_n_en(etype);
+    int64_t* ptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nn + 1));
+    int64_t m = ora_node_graph(nn, ne, ne_n, conn, ptr, NULL, 0);
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    ora_node_graph(nn, ne, ne_n, conn, ptr, idx, m);
+    /* incident-element means of the moduli and the valence */
+    double* smu = (double*)calloc((size_t)nn, sizeof(double));
+    double* slam = (double*)calloc((size_t)nn, sizeof(double));
+    double* val = (double*)calloc((size_t)nn, sizeof(double));
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < ne_n; ++a) {
+            int32_t n = conn[e * ne_n + a];
+            smu[n] += mu[e];
+            slam[n] += lam[e];
+            val[n] += 1.0;
+        }
+    for (int64_t i = 0; i < nn; ++i) {
+        const double* Di = D + i * 9;
+        double s = (Di[0] + Di[4] + Di[8]) / 3.0;
+        double* f = Fo + i * 36;
+        for (int k = 0; k < 9; ++k) f[k] = Di[k] / s;
+        double mean[9] = {0}, dev[9] = {0};
+        int64_t nb = ptr[i + 1] - ptr[i];
+        for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j)
+            for (int k = 0; k < 9; ++k) mean[k] += D[(int64_t)idx[j] * 9 + k];
+        for (int k = 0; k < 9; ++k) mean[k] = nb > 0 ? mean[k] / (double)nb : 0.0;
+        for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j)
+            for (int k = 0; k < 9; ++k) dev[k] += fabs(D[(int64_t)idx[j] * 9 + k] - mean[k]);
+        for (int k = 0; k < 9; ++k) {
+            f[9 + k] = mean[k] / s;
+            f[18 + k] = nb > 0 ? dev[k] / (double)nb / s : 0.0;
+        }
+        double mb = val[i] > 0 ? smu[i] / val[i] : 1.0, lb = val[i] > 0 ? slam[i] / val[i] : 1.0;
+        f[27] = log(mb);
+        f[28] = log(lb / mb);
+        f[29] = val[i] / 24.0;
+        for (int c = 0; c < 3; ++c) {
+            f[30 + c] = mask && mask[i * 3 + c] ? 1.0 : 0.0;
+            f[33 + c] = log(Di[c * 4] / s);
+        }
+    }
+    free(smu);
+    free(slam);
+    free(val);
+    free(idx);
+    free(ptr);
+}
+
+static double softplus(double t) { return t > 30.0 ? t : log1p(exp(t)); }
+
+/* F = C^-T with Dh = C C^T; returns 0 if Dh is not SPD */
+static int lp_factor(const double* Di, double* Fm, double* s_out) {
+    double s = (Di[0] + Di[4] + Di[8]) / 3.0;
+    double A[9], C[9] = {0}, Ci[9] = {0};
+    for (int k = 0; k < 9; ++k) A[k] = Di[k] / s;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double t = A[i * 3 + j];
+            for (int k = 0; k < j; ++k) t -= C[i * 3 + k] * C[j * 3 + k];
+            if (i == j) {
+                if (!(t > 0.0)) return 0;
+                C[i * 3 + i] = sqrt(t);
+            } else {
+                C[i * 3 + j] = t / C[j * 3 + j];
+            }
+        }
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+            double t = (i == j) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= C[i * 3 + k] * Ci[k * 3 + j];
+            Ci[i * 3 + j] = t / C[i * 3 + i];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Fm[i * 3 + j] = Ci[j * 3 + i];
+    *s_out = s;
+    return 1;
+}
+
+static void lp_A(const double* o, double* A) {
+    memset(A, 0, sizeof(double) * 9);
+    A[0] = softplus(o[0]) + 1e-4;
+    A[3] = o[1];
+    A[4] = softplus(o[2]) + 1e-4;
+    A[6] = o[3];
+    A[7] = o[4];
+    A[8] = softplus(o[5]) + 1e-4;
+}
+
+int ora_lp_blocks(int64_t nn, const double* D, const uint8_t* mask, const double* o, double* M) {
+    int ok = 1;
+    for (int64_t i = 0; i < nn; ++i) {
+        double Fm[9], A[9], FA[9], s;
+        double* Mi = M + i * 9;
+        if (!lp_factor(D + i * 9, Fm, &s)) {
+            ok = 0;
+            for (int k = 0; k < 9; ++k) Mi[k] = (k % 4 == 0) ? 1.0 : 0.0;
+            continue;
+        }
+        lp_A(o + i * 6, A);
+        matmul_d(3, Fm, A, FA);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double t = 0.0;
+                for (int k = 0; k < 3; ++k) t += FA[r * 3 + k] * FA[c * 3 + k];
+                Mi[r * 3 + c] = t / s;
+            }
+        for (int c = 0; c < 3; ++c)
+            if (mask && mask[i * 3 + c])
+                for (int k = 0; k < 3; ++k) {
+                    Mi[c * 3 + k] = (k == c) ? 1.0 : 0.0;
+                    Mi[k * 3 + c] = (k == c) ? 1.0 : 0.0;
+                }
+    }
+    return ok;
+}
+
+void ora_lp_blocks_backward(int64_t nn, const double* D, const uint8_t* mask, const double* o,
+                            const double* gM, double* go) {
+    for (int64_t i = 0; i < nn; ++i) {
+        double Fm[9], A[9], G[9], H[9], T[9], W[9], s;
+        double* g = go + i * 6;
+        for (int k = 0; k < 6; ++k) g[k] = 0.0;
+        if (!lp_factor(D + i * 9, Fm, &s)) continue;
+        lp_A(o + i * 6, A);
+        /* the Dirichlet identity rows/columns do not depend on o */
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                int fixed = mask && (mask[i * 3 + r] || mask[i * 3 + c]);
+                G[r * 3 + c] = fixed ? 0.0 : gM[i * 9 + r * 3 + c];
+            }
+        /* dL/dB = F^T G F / s with B = A A^T; dL/dA = (H + H^T) A */
+        double FtG[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double t = 0.0;
+                for (int k = 0; k < 3; ++k) t += Fm[k * 3 + r] * G[k * 3 + c];
+                FtG[r * 3 + c] = t;
+            }
+        matmul_d(3, FtG, Fm, H);
+        for (int k = 0; k < 9; ++k) H[k] /= s;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) T[r * 3 + c] = H[r * 3 + c] + H[c * 3 + r];
+        matmul_d(3, T, A, W);
+        const double sig0 = 1.0 / (1.0 + exp(-o[i * 6 + 0]));
+        const double sig2 = 1.0 / (1.0 + exp(-o[i * 6 + 2]));
+        const double sig5 = 1.0 / (1.0 + exp(-o[i * 6 + 5]));
+        g[0] = W[0] * sig0;
+        g[1] = W[3];
+        g[2] = W[4] * sig2;
+        g[3] = W[6];
+        g[4] = W[7];
+        g[5] = W[8] * sig5;
+    }
+}

@@ -123,6 +123,22 @@ void ora_mlp_backward(int n, int d_in, int h1, int h2, int d_out, const double* 
                       const double* gy, double* gW1, double* gb1, double* gW2,
                       double* gb2, double* gW3, double* gb3, double* gx);
 
+/* Learned block preconditioner (3D).  Node graph: the distinct nodes that
+ * share an element with node i (CSR; idx may be NULL to count).  Returns the
+ * number of entries. */
+int64_t ora_node_graph(int64_t nn, int64_t ne, int n_en, const int32_t* conn, int64_t* ptr,
+                       int32_t* idx, int64_t cap);
+/* 36 features per node from the nodal diagonal blocks D [nn*9] (identity on
+ * prescribed components), the moduli and the per-DOF mask. */
+void ora_lp_features(int etype, int64_t nn, int64_t ne, const int32_t* conn, const double* mu,
+                     const double* lam, const uint8_t* mask, const double* D, double* F);
+/* M_i = F A A^T F^T / s_i from the 6 network outputs per node (see oracle.c);
+ * returns 0 if some D_i is not SPD (that block is set to the identity). */
+int ora_lp_blocks(int64_t nn, const double* D, const uint8_t* mask, const double* o, double* M);
+/* dL/do from dL/dM. */
+void ora_lp_blocks_backward(int64_t nn, const double* D, const uint8_t* mask, const double* o,
+                            const double* gM, double* go);
+
 #ifdef __cplusplus
 }
 #endif

@@ -523,3 +523,94 @@ def test_mlp_special_cases(ora):
     s = lambda t: t / (1 + np.exp(-t))
     y = ora.mlp_forward(x, W1, z(1), W1, z(1), W1, z(1))
     assert y[0, 0] == pytest.approx(s(s(2.0)), rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# learned block preconditioner: node graph, features, SPD blocks
+# ---------------------------------------------------------------------------
+def test_node_graph_brute_force_and_kuhn_counts(ora):
+    m = mg.tet_mesh(3)
+    ptr, idx = ora.node_graph(m.n_nodes, m.conn)
+    nb = [set() for _ in range(m.n_nodes)]
+    for e in m.conn:
+        for a in e:
+            nb[a].update(int(b) for b in e if b != a)
+    for i in range(m.n_nodes):
+        assert list(idx[ptr[i]:ptr[i + 1]]) == sorted(nb[i])
+    # an interior vertex of the Kuhn (Freudenthal) triangulation has 14
+    # neighbours and 24 incident tetrahedra
+    g = mg.grid_index(m)
+    interior = np.all((g > 0) & (g < m.n), axis=1)
+    assert np.all(np.diff(ptr)[interior] == 14)
+    val = np.bincount(m.conn.ravel(), minlength=m.n_nodes)
+    assert np.all(val[interior] == 24)
+
+
+def _spd_blocks(rng, n):
+    B = rng.standard_normal((n, 3, 3))
+    return B @ B.transpose(0, 2, 1) + 0.5 * np.eye(3)
+
+
+def test_lp_blocks_identity_output_is_block_jacobi(ora):
+    rng = np.random.default_rng(5)
+    D = _spd_blocks(rng, 7)
+    o = np.zeros((7, 6))
+    o[:, [0, 2, 5]] = np.log(np.expm1(1.0 - 1e-4))  # softplus(o) + 1e-4 = 1
+    M, ok = ora.lp_blocks(D, None, o)
+    assert ok
+    np.testing.assert_allclose(M, np.linalg.inv(D), rtol=1e-12, atol=1e-14)
+    # a prescribed component gets an identity row and column
+    mask = np.zeros((7, 3), np.uint8)
+    mask[2, 1] = 1
+    Mm, _ = ora.lp_blocks(D, mask, o)
+    assert Mm[2, 1, 1] == 1.0 and Mm[2, 1, 0] == 0.0 and Mm[2, 0, 1] == 0.0
+    np.testing.assert_array_equal(Mm[3], M[3])
+
+
+def test_lp_blocks_are_spd_and_backward_is_fd(ora):
+    rng = np.random.default_rng(6)
+    D = _spd_blocks(rng, 5)
+    o = rng.standard_normal((5, 6))
+    M, ok = ora.lp_blocks(D, None, o)
+    assert ok
+    np.testing.assert_allclose(M, M.transpose(0, 2, 1), atol=1e-13)
+    assert np.all(np.linalg.eigvalsh(M) > 0)
+    mask = np.zeros((5, 3), np.uint8)
+    mask[1, 2] = 1
+    gM = rng.standard_normal((5, 3, 3))
+    go = ora.lp_blocks_backward(D, mask, o, gM)
+    L = lambda oo: np.sum(gM * ora.lp_blocks(D, mask, oo)[0])
+    h = 1e-6
+    for i in range(5):
+        for k in range(6):
+            op, om_ = o.copy(), o.copy()
+            op[i, k] += h
+            om_[i, k] -= h
+            assert (L(op) - L(om_)) / (2 * h) == pytest.approx(go[i, k], rel=1e-6, abs=1e-9)
+
+
+def test_lp_features_invariants(ora):
+    m = mg.bc_base_and_top_3d(mg.tet_mesh(3))
+    mu = np.full(m.n_el, 2.0)
+    lam = 10 * mu
+    D = np.tile(3.0 * np.eye(3), (m.n_nodes, 1, 1))  # every block the same
+    F = ora.lp_features(m.elem_type, m.conn, mu, lam, m.dirichlet, D)
+    assert F.shape == (m.n_nodes, 36)
+    np.testing.assert_allclose(F[:, 0:9], np.tile(np.eye(3).ravel(), (m.n_nodes, 1)))
+    np.testing.assert_allclose(F[:, 9:18], F[:, 0:9])       # neighbour mean = own block
+    np.testing.assert_allclose(F[:, 18:27], 0.0, atol=0)     # no spread
+    np.testing.assert_allclose(F[:, 27], np.log(2.0))
+    np.testing.assert_allclose(F[:, 28], np.log(10.0))
+    val = np.bincount(m.conn.ravel(), minlength=m.n_nodes)
+    np.testing.assert_allclose(F[:, 29], val / 24.0)
+    np.testing.assert_array_equal(F[:, 30:33], m.dirichlet)
+    np.testing.assert_allclose(F[:, 33:36], 0.0, atol=1e-15)  # log(diag / s) = log 1
+    # a block twice as stiff at one node: its neighbours see the spread
+    D2 = D.copy()
+    D2[0] *= 2.0
+    F2 = ora.lp_features(m.elem_type, m.conn, mu, lam, m.dirichlet, D2)
+    np.testing.assert_allclose(F2[0, 0:9], F[0, 0:9])         # normalised by its own trace
+    ptr, idx = ora.node_graph(m.n_nodes, m.conn)
+    j = idx[ptr[0]]
+    nbj = ptr[j + 1] - ptr[j]
+    assert F2[j, 9] == pytest.approx(1.0 + 1.0 / nbj)         # mean of D_00 / s_j
