@@ -250,6 +250,7 @@ fem_status fem_param_vjp(fem_mesh* mesh, int dtype, const void* u, const void* a
  * diagonal block of fem_block_diag inverted through its Cholesky factor).
  * ------------------------------------------------------------------------ */
 #define FEM_PC_BLOCK_JACOBI 0
+#define FEM_PC_LEARNED 1 /* the learned block preconditioner (fem_lp_*); FP32 CG, 3D */
 
 typedef struct {
     int32_t cg_dtype;      /* FEM_F64: the PCG, its HVPs and preconditioner in
@@ -270,6 +271,7 @@ typedef struct {
                               the device-side stop flag (0 = 8); iterations
                               past the stop are skipped on the device, so the
                               result does not depend on it                   */
+    const void* learned;   /* fem_lp* when precond == FEM_PC_LEARNED, else NULL */
 } fem_newton_opts;
 
 typedef struct {
@@ -321,6 +323,67 @@ fem_status fem_newton_step(fem_mesh* mesh, double* u, const double* ubar, double
  */
 fem_status fem_tangent_solve(fem_mesh* mesh, int cg_dtype, const double* u, const double* b, double* x,
                              double rtol, int64_t cg_max, int64_t* iters, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned block preconditioner (3D meshes created FEM_PREC_MIXED; the PCG of
+ * fem_newton_step with cg_dtype FEM_F32 and precond FEM_PC_LEARNED).
+ *
+ * The paper has no preconditioner of this kind; it is the learned part of
+ * this implementation.  A per-node MLP 36 -> 64 -> 64 -> 6 (SiLU hidden
+ * layers; BF16 weights and activations, FP32 accumulation, tensor cores)
+ * corrects block Jacobi: with D_i the nodal diagonal block, s_i = tr(D_i)/3,
+ * D_i / s_i = C C^T and F = C^-T, the preconditioner block is
+ *     M_i = F A A^T F^T / s_i,
+ * A lower-triangular from the 6 outputs (softplus(o) + 1e-4 on its
+ * diagonal).  M_i is SPD for any weights and is block Jacobi D_i^-1 for
+ * A = I, the network fem_lp_create starts from.  Prescribed components get
+ * identity rows and columns.  Features per node (36): D_i / s_i (9); the mean
+ * of the neighbours' D_j / s_i (9); their mean absolute deviation / s_i (9);
+ * ln of the mean incident mu, ln(mean lambda / mean mu), valence / 24 (3);
+ * the Dirichlet bits (3); ln(D_i,cc / s_i) (3).  Neighbours share an element.
+ * Training minimises ||H M r - r||^2 / ||r||^2 with H = M K(u) M (masked)
+ * over states and residuals supplied by the caller (one Adam step per call;
+ * the gradient needs a second HVP).  The first call on a mesh builds its node
+ * graph (host) and allocates a workspace kept until fem_mesh_destroy.
+ * Parameters (FEM_LP_PARAMS floats): W1[64][36], b1[64], W2[64][64], b2[64],
+ * W3[6][64], b3[6], row-major W[out][in].
+ * ------------------------------------------------------------------------ */
+#define FEM_LP_FEATURES 36
+#define FEM_LP_PARAMS 6918
+typedef struct fem_lp fem_lp;
+
+/* New network (W1, W2 ~ N(0, 1/fan_in) from a SplitMix64 stream of `seed`,
+ * W3 = 0, biases giving A = I: block Jacobi). */
+fem_status fem_lp_create(uint64_t seed, fem_lp** out);
+fem_status fem_lp_destroy(fem_lp* lp);
+/* Training loss: FEM_LP_LOSS_RESIDUAL (the default) ||H M r - r||^2 / ||r||^2,
+ * whose gradient in z = M r is 2 H (H z - r) / ||r||^2 (a second HVP); or
+ * FEM_LP_LOSS_ENERGY, the same residual measured in the H^-1 norm,
+ * (r - H z)^T H^-1 (r - H z) / ||r||^2, reported shifted by the constant
+ * r^T H^-1 r / ||r||^2 (1 + (z^T H z - 2 r^T z) / ||r||^2), gradient
+ * 2 (H z - r) / ||r||^2.  For r with identity covariance the energy loss is
+ * minimised over block-diagonal M exactly by block Jacobi. */
+#define FEM_LP_LOSS_RESIDUAL 0
+#define FEM_LP_LOSS_ENERGY 1
+fem_status fem_lp_set_loss(fem_lp* lp, int kind);
+/* HOST float[FEM_LP_PARAMS] out / in (set also resets the Adam state). */
+fem_status fem_lp_get_params(const fem_lp* lp, float* params);
+fem_status fem_lp_set_params(fem_lp* lp, const float* params);
+/* Features at the FP32 state u: X DEVICE bf16 [n_nodes * 48] (36 used, the
+ * rest zero). */
+fem_status fem_lp_features(fem_mesh* mesh, const float* u, void* X, void* stream);
+/* Preconditioner blocks at the FP32 state u: Minv DEVICE float [n_nodes * 9]. */
+fem_status fem_lp_blocks(const fem_lp* lp, fem_mesh* mesh, const float* u, float* Minv, void* stream);
+/* Loss at (u, r) (DEVICE float [n_nodes * 3] each, r masked) and its
+ * gradient in the parameters: grad HOST float[FEM_LP_PARAMS]; *loss HOST
+ * (may be NULL).  Synchronises `stream`; changes nothing. */
+fem_status fem_lp_gradient(fem_lp* lp, fem_mesh* mesh, const float* u, const float* r, float* grad,
+                           double* loss, void* stream);
+/* One Adam step (learning rate lr) on the loss at (u, r), both DEVICE float
+ * [n_nodes * 3], r masked; *loss (HOST, may be NULL: no synchronisation)
+ * receives the loss before the step. */
+fem_status fem_lp_train_step(fem_lp* lp, fem_mesh* mesh, const float* u, const float* r, float lr,
+                             double* loss, void* stream);
 
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */

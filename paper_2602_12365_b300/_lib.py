@@ -42,14 +42,16 @@ class MeshInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-FEM_PC_BLOCK_JACOBI = 0
+FEM_PC_BLOCK_JACOBI, FEM_PC_LEARNED = 0, 1
+FEM_LP_FEATURES, FEM_LP_PARAMS = 36, 6918
+FEM_LP_LOSS_RESIDUAL, FEM_LP_LOSS_ENERGY = 0, 1
 
 
 class NewtonOpts(C.Structure):
     _fields_ = [("cg_dtype", C.c_int32), ("precond", C.c_int32), ("newton_rtol", C.c_double),
                 ("newton_max", C.c_int32), ("ls_max", C.c_int32), ("eta_max", C.c_double),
                 ("cg_max", C.c_int64), ("predictor_rtol", C.c_double), ("armijo_c", C.c_double),
-                ("max_bisect", C.c_int32), ("cg_batch", C.c_int32)]
+                ("max_bisect", C.c_int32), ("cg_batch", C.c_int32), ("learned", C.c_void_p)]
 
 
 class NewtonStats(C.Structure):
@@ -95,6 +97,15 @@ def lib():
             "fem_sync_status": [P, P, C.POINTER(i32)],
             "fem_newton_default_opts": [C.POINTER(NewtonOpts)],
             "fem_tangent_solve": [P, i32, P, P, P, C.c_double, C.c_int64, C.POINTER(C.c_int64), P],
+            "fem_lp_create": [C.c_uint64, C.POINTER(C.c_void_p)],
+            "fem_lp_destroy": [P],
+            "fem_lp_set_loss": [P, i32],
+            "fem_lp_get_params": [P, P],
+            "fem_lp_set_params": [P, P],
+            "fem_lp_features": [P, P, P, P],
+            "fem_lp_blocks": [P, P, P, P, P],
+            "fem_lp_train_step": [P, P, P, P, C.c_float, C.POINTER(C.c_double), P],
+            "fem_lp_gradient": [P, P, P, P, P, C.POINTER(C.c_double), P],
             "fem_newton_step": [P, P, P, C.c_double, C.c_double, C.POINTER(NewtonOpts),
                                 C.POINTER(NewtonStats), P],
         }
@@ -115,4 +126,6 @@ def check(status: int):
 EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_plan_partition",
             "fem_energy", "fem_energy_static", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
             "fem_sync_status", "fem_newton_default_opts", "fem_newton_step", "fem_tangent_solve",
+            "fem_lp_create", "fem_lp_destroy", "fem_lp_set_loss", "fem_lp_get_params", "fem_lp_set_params",
+            "fem_lp_features", "fem_lp_blocks", "fem_lp_gradient", "fem_lp_train_step",
             "fem_last_error"]

@@ -509,6 +509,28 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
     m->mu0 = d->mu0;
     m->lam0 = d->lambda0;
     const bool mixed = d->precision == FEM_PREC_MIXED;
+    if (d->n_nodes > 0 && d->n_elems > 0 && d->conn) {
+        // host data of the learned preconditioner (one pass over the elements)
+        const int ne_n = nen_of(d->elem_type);
+        m->conn_host.assign(d->conn, d->conn + d->n_elems * ne_n);
+        std::vector<double> smu((size_t)d->n_nodes, 0.0), slam((size_t)d->n_nodes, 0.0), val((size_t)d->n_nodes, 0.0);
+        for (int64_t e = 0; e < d->n_elems; ++e)
+            for (int a = 0; a < ne_n; ++a) {
+                const int32_t n = d->conn[e * ne_n + a];
+                if (n < 0 || n >= d->n_nodes) continue;  // rejected by the planner below
+                smu[n] += d->mu ? d->mu[e] : d->mu0;
+                slam[n] += d->lambda ? d->lambda[e] : d->lambda0;
+                val[n] += 1.0;
+            }
+        m->node_stats.resize((size_t)d->n_nodes * 3);
+        for (int64_t n = 0; n < d->n_nodes; ++n) {
+            const double mb = val[n] > 0 ? smu[n] / val[n] : d->mu0;
+            const double lb = val[n] > 0 ? slam[n] / val[n] : d->lambda0;
+            m->node_stats[n * 3 + 0] = (float)std::log(mb);
+            m->node_stats[n * 3 + 1] = (float)std::log(lb / mb);
+            m->node_stats[n * 3 + 2] = (float)(val[n] / 24.0);
+        }
+    }
     // plan; halve the tile until its shared memory fits the device
     int tile = d->tile_elems;
     fem_status s;
@@ -637,6 +659,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaDeviceSynchronize();
     femi::solver_free(m);
+    femi::lp_mesh_free(m);
     free_all(m);
     delete m;
     return FEM_OK;

@@ -11,6 +11,7 @@
 
 namespace femi {
 struct SolverWork;  // Newton-CG workspace, created on first use (fem_solver.cu)
+struct LpMeshData;  // learned-preconditioner graph on the device (fem_learned.cu)
 }
 
 struct fem_mesh {
@@ -48,6 +49,12 @@ struct fem_mesh {
     int* status = nullptr;
     // Newton-CG workspace (allocated by the first fem_newton_step)
     femi::SolverWork* solver = nullptr;
+    // host data of the learned preconditioner: the connectivity (its node
+    // graph is built on first use) and per-node statistics (ln of the mean
+    // incident mu, ln(mean lambda / mean mu), valence / 24)
+    std::vector<int32_t> conn_host;
+    std::vector<float> node_stats;
+    femi::LpMeshData* lp = nullptr;
 };
 
 namespace femi {
@@ -59,4 +66,10 @@ fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
                   double* out_scalar, unsigned flags, cudaStream_t st, const int* skip);
 // frees the Newton-CG workspace of `m` (no-op without one)
 void solver_free(fem_mesh* m);
+// frees the learned-preconditioner data of `m` (no-op without it)
+void lp_mesh_free(fem_mesh* m);
+// fills the CG preconditioner blocks Minv [n_nodes * 9] (FP32) from the
+// learned network `lp` at the FP32 state u: block diagonal, features,
+// network, SPD map (fem_learned.cu)
+fem_status lp_precondition(const void* lp, fem_mesh* m, const float* u, float* Minv, cudaStream_t st);
 }  // namespace femi

@@ -694,8 +694,14 @@ private:
         return w_->u32;
     }
 
-    // block-Jacobi preconditioner at u; returns 5 when a block is not SPD
+    // block-Jacobi (or learned) preconditioner at u; returns 5 when a block
+    // is not SPD
     int build_block_jacobi(const void* ucg, fem_status* err) {
+        if (o_.precond == FEM_PC_LEARNED) {
+            *err = femi::lp_precondition(o_.learned, m_, static_cast<const float*>(ucg),
+                                         static_cast<float*>(w_->Minv[1]), st_);
+            return *err == FEM_OK ? 0 : -1;
+        }
         *err = femi::run_op(m_, dt_, fem::OP_BLOCKDIAG, ucg, nullptr, w_->Db[pi_], nullptr, 0, st_, nullptr);
         if (*err != FEM_OK) return -1;
         if (cudaMemsetAsync(w_->bad, 0, sizeof(int), st_) != cudaSuccess) {
@@ -930,6 +936,7 @@ fem_status fem_newton_default_opts(fem_newton_opts* o) {
     o->ls_max = 20;
     o->max_bisect = 5;
     o->cg_batch = 8;
+    o->learned = nullptr;
     return FEM_OK;
 }
 
@@ -944,7 +951,9 @@ fem_status fem_newton_step(fem_mesh* m, double* u, const double* ubar, double s_
     if (o.cg_dtype != FEM_F64 && o.cg_dtype != FEM_F32) return fail(FEM_ERR_ARG, "cg_dtype must be FEM_F64 or FEM_F32");
     if (o.cg_dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
         return fail(FEM_ERR_ARG, "cg_dtype FEM_F32 needs a mesh created with FEM_PREC_MIXED");
-    if (o.precond != FEM_PC_BLOCK_JACOBI) return fail(FEM_ERR_ARG, "unknown preconditioner");
+    if (o.precond != FEM_PC_BLOCK_JACOBI && o.precond != FEM_PC_LEARNED) return fail(FEM_ERR_ARG, "unknown preconditioner");
+    if (o.precond == FEM_PC_LEARNED && (o.cg_dtype != FEM_F32 || m->dim != 3 || !o.learned))
+        return fail(FEM_ERR_ARG, "FEM_PC_LEARNED needs cg_dtype FEM_F32, a 3D mesh and a fem_lp handle");
     if (o.newton_max < 0 || o.ls_max < 0 || o.max_bisect < 0 || o.cg_max < 0)
         return fail(FEM_ERR_ARG, "negative iteration limit");
     if (!(s >= s_prev) || !std::isfinite(s) || !std::isfinite(s_prev)) return fail(FEM_ERR_ARG, "need finite s >= s_prev");

@@ -187,8 +187,9 @@ class Mesh:
                     **opts):
         """One Newton-CG load step from s_prev to s (fem_newton_step); u (FP64,
         on the device) is updated in place.  ``cg_dtype`` float32 runs the PCG
-        in FP32 with FP64 dots; keyword ``opts`` override fem_newton_opts
-        fields.  Returns the step statistics as a dict; with ``check`` a
+        in FP32 with FP64 dots; ``learned=`` a LearnedPreconditioner selects
+        the learned block preconditioner; other keyword ``opts`` override
+        fem_newton_opts fields.  Returns the step statistics as a dict; with ``check`` a
         failed step raises FemError."""
         if u.dtype != torch.float64 or ubar.dtype != torch.float64:
             raise TypeError("u and ubar must be float64 (the master state is FP64)")
@@ -196,6 +197,10 @@ class Mesh:
         o = L.NewtonOpts()
         L.check(L.lib().fem_newton_default_opts(C.byref(o)))
         o.cg_dtype = L.FEM_F64 if cg_dtype == torch.float64 else L.FEM_F32
+        learned = opts.pop("learned", None)
+        if learned is not None:  # a LearnedPreconditioner
+            o.precond = L.FEM_PC_LEARNED
+            o.learned = learned.handle.value
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")

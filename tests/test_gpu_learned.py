@@ -1,0 +1,178 @@
+"""Learned block preconditioner on the GPU against the oracle.
+
+Precision bars.  Features are FP32 from an FP32 block diagonal, stored as
+BF16: within two BF16 ulps (2^-7 relative) plus 1e-3 absolute of the FP64
+oracle.  The network runs on BF16 weights (the oracle receives the same
+BF16-rounded weights and inputs) and BF16 hidden activations (the oracle keeps
+them in FP64): one BF16 rounding per layer of O(1) activations bounds the
+output error at a few 2^-9, so the blocks match to 3e-2 and the weight
+gradients to 5e-2 relative.  The untrained network has W3 = 0, so its output
+is exactly the bias and its blocks are block Jacobi to FP32 rounding (1e-5).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_12365_b300 import meshgen as mg
+from paper_2602_12365_b300._lib import FemError
+from paper_2602_12365_b300.fem import Mesh
+from paper_2602_12365_b300.learned import (LearnedPreconditioner, load_path_samples, sample_loss,
+                                           train)
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    return torch.as_tensor(np.asarray(a, np.float64)).to(torch.bfloat16).double().numpy()
+
+
+def _case(n=6, seed=3):
+    m = mg.workload_tet(n, seed=seed, random_moduli=seed)
+    gm = Mesh.from_fixture(m)
+    u32 = torch.as_tensor(mg.smooth_state(m, 0.5, amp=0.03).ravel(), dtype=torch.float32, device="cuda")
+    om = oracle.OracleMesh.from_mesh(m)
+    u64 = u32.double().cpu().numpy()  # the oracle sees the FP32 state the kernels see
+    D = om.block_diag(u64).reshape(-1, 3, 3)
+    return m, gm, u32, om, u64, D
+
+
+def _perturbed(seed=5, scale=0.05):
+    lp = LearnedPreconditioner(seed)
+    p = lp.params()
+    rng = np.random.default_rng(seed)
+    W1, b1, W2, b2, W3, b3 = LearnedPreconditioner.unpack(p)
+    W3[:] = scale * rng.standard_normal(W3.shape)
+    b1[:] = 0.1 * rng.standard_normal(b1.shape)
+    b3[:] += 0.1 * rng.standard_normal(b3.shape)
+    lp.set_params(p)
+    return lp
+
+
+def _oracle_net(lp, m, D):
+    """features (oracle), BF16 inputs and weights, FP64 MLP -> outputs o"""
+    F = oracle.lp_features(m.elem_type, m.conn, m.mu_e(), m.lam_e(), m.dirichlet, D)
+    W = [_bf16(w) if w.ndim == 2 else np.asarray(w, np.float64)
+         for w in LearnedPreconditioner.unpack(lp.params())]
+    return F, W, oracle.mlp_forward(_bf16(F), *W)
+
+
+def test_features_match_oracle():
+    m, gm, u32, _, _, D = _case()
+    X = LearnedPreconditioner.features(gm, u32).float().cpu().numpy()
+    F = oracle.lp_features(m.elem_type, m.conn, m.mu_e(), m.lam_e(), m.dirichlet, D)
+    assert np.all(X[:, 36:] == 0)
+    err = np.abs(X[:, :36] - F)
+    assert np.all(err <= 2.0 ** -7 * np.abs(F) + 1e-3), err.max()
+
+
+def test_untrained_network_is_block_jacobi():
+    m, gm, u32, _, _, D = _case()
+    lp = LearnedPreconditioner(7)
+    M = lp.blocks(gm, u32).double().cpu().numpy()
+    o0 = np.tile(LearnedPreconditioner.unpack(lp.params())[5], (m.n_nodes, 1))
+    Mo, ok = oracle.lp_blocks(D, m.dirichlet, o0)
+    assert ok
+    assert np.linalg.norm(M - Mo) / np.linalg.norm(Mo) <= 1e-5
+    free = ~np.any(m.dirichlet.astype(bool), axis=1)
+    Dinv = np.linalg.inv(D[free])
+    assert np.linalg.norm(M[free] - Dinv) / np.linalg.norm(Dinv) <= 1e-5
+
+
+def test_blocks_match_oracle():
+    m, gm, u32, _, _, D = _case()
+    lp = _perturbed()
+    M = lp.blocks(gm, u32).double().cpu().numpy()
+    _, _, o = _oracle_net(lp, m, D)
+    Mo, ok = oracle.lp_blocks(D, m.dirichlet, o)
+    assert ok
+    assert np.linalg.norm(M - Mo) / np.linalg.norm(Mo) <= 3e-2
+    np.testing.assert_allclose(M, M.transpose(0, 2, 1), atol=1e-6 * np.abs(M).max())
+    assert np.all(np.linalg.eigvalsh(M) > 0)
+
+
+@pytest.mark.parametrize("loss", ["residual", "energy"])
+def test_gradient_matches_oracle(loss):
+    m, gm, u32, om, u64, D = _case()
+    lp = _perturbed()
+    lp.set_loss(loss)
+    r = om.residual(u64, mask_out=True)
+    r32 = torch.as_tensor(r, dtype=torch.float32, device="cuda")
+    r = r32.double().cpu().numpy()
+    lval, g = lp.gradient(gm, u32, r32)
+    # the same chain on the oracle
+    F, W, o = _oracle_net(lp, m, D)
+    Mo, _ = oracle.lp_blocks(D, m.dirichlet, o)
+    z = np.einsum("nij,nj->ni", Mo, r.reshape(-1, 3)).ravel()
+    q = om.hvp(u64, z)
+    e = q - r
+    rr = r @ r
+    if loss == "residual":
+        lo = e @ e / rr
+        gz = 2.0 * om.hvp(u64, e) / rr
+    else:
+        lo = 1.0 + (z @ q - 2.0 * r @ z) / rr
+        gz = 2.0 * e / rr
+    gM = np.einsum("ni,nj->nij", gz.reshape(-1, 3), r.reshape(-1, 3))
+    go = oracle.lp_blocks_backward(D, m.dirichlet, o, gM)
+    grads, _ = oracle.mlp_backward(_bf16(F), *W, go)
+    go_flat = np.concatenate([a.ravel() for a in grads])
+    assert lval == pytest.approx(lo, rel=1e-2)
+    assert np.linalg.norm(g - go_flat) / np.linalg.norm(go_flat) <= 5e-2
+
+
+def test_training_lowers_the_loss_and_the_solve_is_unchanged():
+    """What the trained network gains: training lowers its loss on the
+    method's own Newton residuals.  The PCG with the learned blocks converges
+    to the block-Jacobi solution; the CG iteration counts of both are
+    reported (a block-diagonal preconditioner cannot shorten CG much: block
+    Jacobi is already optimal among them by Kaporin's condition number)."""
+    ds = []
+    for sd in (1, 2):
+        m = mg.workload_tet(8, seed=sd, random_moduli=sd)
+        gm = Mesh.from_fixture(m)
+        ds.append((gm, load_path_samples(gm, m, 3)))
+    lp = LearnedPreconditioner(0)
+    before = sample_loss(lp, ds)
+    train(lp, ds, epochs=15, lr=2e-3)
+    after = sample_loss(lp, ds)
+    assert after < 0.8 * before
+    m = mg.workload_tet(8, seed=9, random_moduli=9)
+    gm = Mesh.from_fixture(m)
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    res = {}
+    for arm, kw in (("block_jacobi", {}), ("learned", {"learned": lp})):
+        u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device="cuda")
+        st = gm.newton_step(u, ubar, 0.0, 0.05, cg_dtype=torch.float32, **kw)
+        assert st["status"] == 0 and st["r_norm"] <= 1e-8 * st["r0_norm"]
+        res[arm] = (u, st["cg_iters"])
+    ub, ul = res["block_jacobi"][0], res["learned"][0]
+    assert (torch.linalg.norm(ul - ub) / torch.linalg.norm(ub)).item() <= 1e-6
+    print(f"loss {before:.4f} -> {after:.4f}; CG iterations block Jacobi {res['block_jacobi'][1]}, "
+          f"learned {res['learned'][1]}")
+
+
+def test_untrained_learned_solve_matches_block_jacobi_iterations():
+    m = mg.workload_tet(8, seed=4, random_moduli=4)
+    gm = Mesh.from_fixture(m)
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    its = []
+    for kw in ({}, {"learned": LearnedPreconditioner(3)}):
+        u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device="cuda")
+        st = gm.newton_step(u, ubar, 0.0, 0.05, cg_dtype=torch.float32, **kw)
+        assert st["status"] == 0
+        its.append(st["cg_iters"])
+    assert abs(its[0] - its[1]) <= max(2, 0.02 * its[0])
+
+
+def test_learned_needs_fp32_cg_and_3d():
+    m = mg.workload_tet(3)
+    gm = Mesh.from_fixture(m)
+    u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device="cuda")
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device="cuda")
+    with pytest.raises(FemError, match="FEM_PC_LEARNED"):
+        gm.newton_step(u, ubar, 0.0, 0.1, cg_dtype=torch.float64, learned=LearnedPreconditioner(0))
+    m2 = mg.workload_tri(4)
+    g2 = Mesh.from_fixture(m2)
+    with pytest.raises(FemError, match="3D"):
+        LearnedPreconditioner(0).blocks(g2, torch.zeros(m2.n_nodes * 2, dtype=torch.float32, device="cuda"))
