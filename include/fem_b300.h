@@ -338,7 +338,8 @@ fem_status fem_tangent_solve(fem_mesh* mesh, int cg_dtype, const double* u, cons
  * diagonal).  M_i is SPD for any weights and is block Jacobi D_i^-1 for
  * A = I, the network fem_lp_create starts from.  Prescribed components get
  * identity rows and columns.  Features per node (36): D_i / s_i (9); the mean
- * of the neighbours' D_j / s_i (9); their mean absolute deviation / s_i (9);
+ * of the neighbours' D_j / s_i (9); their mean absolute deviation / s_i (9)
+ * (these 27 compressed as sign(x) ln(1 + |x|));
  * ln of the mean incident mu, ln(mean lambda / mean mu), valence / 24 (3);
  * the Dirichlet bits (3); ln(D_i,cc / s_i) (3).  Neighbours share an element.
  * Training minimises ||H M r - r||^2 / ||r||^2 with H = M K(u) M (masked)
@@ -366,6 +367,9 @@ fem_status fem_lp_destroy(fem_lp* lp);
 #define FEM_LP_LOSS_RESIDUAL 0
 #define FEM_LP_LOSS_ENERGY 1
 fem_status fem_lp_set_loss(fem_lp* lp, int kind);
+/* Adam steps scale the gradient to at most this 2-norm (default 1; 0 = no
+ * clipping). */
+fem_status fem_lp_set_clip(fem_lp* lp, float max_grad_norm);
 /* HOST float[FEM_LP_PARAMS] out / in (set also resets the Adam state). */
 fem_status fem_lp_get_params(const fem_lp* lp, float* params);
 fem_status fem_lp_set_params(fem_lp* lp, const float* params);

@@ -831,6 +831,9 @@ void ora_lp_features(int etype, int64_t nn, int64_t ne, const int32_t* conn, con
             f[9 + k] = mean[k] / s;
             f[18 + k] = nb > 0 ? dev[k] / (double)nb / s : 0.0;
         }
+        /* block ratios span orders of magnitude at boundary and
+           high-contrast nodes: compress them as sign(x) ln(1 + |x|) */
+        for (int k = 0; k < 27; ++k) f[k] = copysign(log1p(fabs(f[k])), f[k]);
         double mb = val[i] > 0 ? smu[i] / val[i] : 1.0, lb = val[i] > 0 ? slam[i] / val[i] : 1.0;
         f[27] = log(mb);
         f[28] = log(lb / mb);

@@ -129,7 +129,8 @@ void ora_mlp_backward(int n, int d_in, int h1, int h2, int d_out, const double* 
 int64_t ora_node_graph(int64_t nn, int64_t ne, int n_en, const int32_t* conn, int64_t* ptr,
                        int32_t* idx, int64_t cap);
 /* 36 features per node from the nodal diagonal blocks D [nn*9] (identity on
- * prescribed components), the moduli and the per-DOF mask. */
+ * prescribed components), the moduli and the per-DOF mask; the 27 block
+ * features are compressed as sign(x) ln(1 + |x|). */
 void ora_lp_features(int etype, int64_t nn, int64_t ne, const int32_t* conn, const double* mu,
                      const double* lam, const uint8_t* mask, const double* D, double* F);
 /* M_i = F A A^T F^T / s_i from the 6 network outputs per node (see oracle.c);

@@ -100,6 +100,7 @@ def lib():
             "fem_lp_create": [C.c_uint64, C.POINTER(C.c_void_p)],
             "fem_lp_destroy": [P],
             "fem_lp_set_loss": [P, i32],
+            "fem_lp_set_clip": [P, C.c_float],
             "fem_lp_get_params": [P, P],
             "fem_lp_set_params": [P, P],
             "fem_lp_features": [P, P, P, P],
@@ -126,6 +127,7 @@ def check(status: int):
 EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_plan_partition",
             "fem_energy", "fem_energy_static", "fem_residual", "fem_hvp", "fem_block_diag", "fem_param_vjp",
             "fem_sync_status", "fem_newton_default_opts", "fem_newton_step", "fem_tangent_solve",
-            "fem_lp_create", "fem_lp_destroy", "fem_lp_set_loss", "fem_lp_get_params", "fem_lp_set_params",
+            "fem_lp_create", "fem_lp_destroy", "fem_lp_set_loss", "fem_lp_set_clip",
+            "fem_lp_get_params", "fem_lp_set_params",
             "fem_lp_features", "fem_lp_blocks", "fem_lp_gradient", "fem_lp_train_step",
             "fem_last_error"]

@@ -191,6 +191,7 @@ __device__ __forceinline__ void lp_block(const float (&Di)[9], uint8_t mask, con
 //   [0,9)   D_i / s_i
 //   [9,18)  mean over neighbour nodes of D_j, / s_i
 //   [18,27) mean absolute deviation of the neighbours' D_j, / s_i
+//           (these 27 compressed as sign(x) ln(1 + |x|))
 //   27 ln mean mu, 28 ln(mean lambda / mean mu), 29 valence / 24
 //   [30,33) Dirichlet bits, [33,36) ln(D_i,cc / s_i)
 // ---------------------------------------------------------------------------
@@ -226,6 +227,10 @@ __global__ void __launch_bounds__(kVecT) lp_features_kernel(int64_t nn, const fl
             f[9 + k] = mean[k] * is;
             f[18 + k] = dev[k] * inb * is;
         }
+        // block ratios span orders of magnitude at boundary and
+        // high-contrast nodes: compress them as sign(x) ln(1 + |x|)
+#pragma unroll
+        for (int k = 0; k < 27; ++k) f[k] = copysignf(log1pf(fabsf(f[k])), f[k]);
         f[27] = stats[n * 3 + 0];
         f[28] = stats[n * 3 + 1];
         f[29] = stats[n * 3 + 2];
@@ -631,12 +636,30 @@ __global__ void lp_sum_kernel(int nb, const float* partial, float* grad) {
     grad[p] = g;
 }
 
-// Adam on the FP32 master weights, then their BF16 inference copy
-__global__ void lp_adam_kernel(const float* grad, float* w, float* m, float* v, float lr, float b1, float b2,
-                               float eps, float c1, float c2, __nv_bfloat16* wb, float* bb) {
+// one block: the gradient's 2-norm (fixed order) and the clipping factor
+// min(1, clip / ||g||)
+__global__ void lp_clip_kernel(const float* grad, float clip, float* scale) {
+    __shared__ double sh[kVecT / 32];
+    double a = 0.0;
+    for (int p = threadIdx.x; p < kParams; p += kVecT) a = fma((double)grad[p], (double)grad[p], a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kVecT / 32; ++w) a += sh[w];
+        const double nrm = sqrt(a);
+        *scale = (clip > 0.0f && nrm > (double)clip) ? (float)((double)clip / nrm) : 1.0f;
+    }
+}
+
+// Adam on the FP32 master weights (gradient scaled by the clipping factor),
+// then their BF16 inference copy
+__global__ void lp_adam_kernel(const float* grad, const float* scale, float* w, float* m, float* v, float lr,
+                               float b1, float b2, float eps, float c1, float c2, __nv_bfloat16* wb, float* bb) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= kParams) return;
-    const float g = grad[p];
+    const float g = grad[p] * *scale;
     const float mm = b1 * m[p] + (1.f - b1) * g;
     const float vv = b2 * v[p] + (1.f - b2) * g * g;
     m[p] = mm;
@@ -669,6 +692,7 @@ struct fem_lp {
     int64_t step = 0;
     int device = 0;
     int loss = FEM_LP_LOSS_RESIDUAL;
+    float clip = 1.0f;  // gradient-norm clipping threshold (0: none)
 };
 
 namespace femi {
@@ -681,7 +705,7 @@ struct LpMeshData {
     __nv_bfloat16* X = nullptr;
     float *Minv = nullptr, *z = nullptr, *q = nullptr, *e = nullptr;
     float* partial = nullptr;  // [kGradBlocks * kParams]
-    float* grad = nullptr;     // [kParams]
+    float* grad = nullptr;     // [kParams], then the clipping factor
     double* red = nullptr;     // [kRedBlocks * 4 + 3]
     std::vector<void*> allocs;
 };
@@ -748,7 +772,7 @@ fem_status ensure_mesh(fem_mesh* m, cudaStream_t st) {
     FEM_TRY(dalloc(d, &d->q, (size_t)nn * 3));
     FEM_TRY(dalloc(d, &d->e, (size_t)nn * 3));
     FEM_TRY(dalloc(d, &d->partial, (size_t)kGradBlocks * kParams));
-    FEM_TRY(dalloc(d, &d->grad, (size_t)kParams));
+    FEM_TRY(dalloc(d, &d->grad, (size_t)kParams + 1));
     FEM_TRY(dalloc(d, &d->red, (size_t)kRedBlocks * 4 + 3));
     CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
     return FEM_OK;
@@ -873,6 +897,13 @@ fem_status fem_lp_set_loss(fem_lp* lp, int kind) {
     return FEM_OK;
 }
 
+fem_status fem_lp_set_clip(fem_lp* lp, float max_grad_norm) {
+    FEM_TRY(check_lp(lp));
+    if (!(max_grad_norm >= 0.0f)) return fail(FEM_ERR_ARG, "need max_grad_norm >= 0");
+    lp->clip = max_grad_norm;
+    return FEM_OK;
+}
+
 fem_status fem_lp_get_params(const fem_lp* lp, float* params) {
     FEM_TRY(check_lp(lp));
     if (!params) return fail(FEM_ERR_ARG, "null parameter buffer");
@@ -972,8 +1003,10 @@ fem_status fem_lp_train_step(fem_lp* lp, fem_mesh* m, const float* u, const floa
     ++lp->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)lp->step), c2 = 1.0f - std::pow(b2, (float)lp->step);
-    lp_adam_kernel<<<(kParams + 255) / 256, 256, 0, st>>>(m->lp->grad, lp->w, lp->m, lp->v, lr, b1, b2, 1e-8f, c1,
-                                                          c2, lp->wb, lp->bb);
+    float* scale = m->lp->grad + kParams;
+    lp_clip_kernel<<<1, kVecT, 0, st>>>(m->lp->grad, lp->clip, scale);
+    lp_adam_kernel<<<(kParams + 255) / 256, 256, 0, st>>>(m->lp->grad, scale, lp->w, lp->m, lp->v, lr, b1, b2, 1e-8f,
+                                                          c1, c2, lp->wb, lp->bb);
     CUDA_TRY(cudaGetLastError());
     if (loss) return read_loss(loss3, loss, st);
     return FEM_OK;

@@ -43,6 +43,10 @@ class LearnedPreconditioner:
         L.check(L.lib().fem_lp_set_loss(self._h, kind))
         self.loss = loss
 
+    def set_clip(self, max_grad_norm: float) -> None:
+        """Gradient-norm clipping of the Adam steps (0: none)."""
+        L.check(L.lib().fem_lp_set_clip(self._h, C.c_float(max_grad_norm)))
+
     def close(self):
         if getattr(self, "_h", None):
             L.lib().fem_lp_destroy(self._h)
