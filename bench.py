@@ -16,7 +16,8 @@ stream the kernels run on.
 The line also carries the Newton-CG measurement ("newton"): seconds per load
 step to relative residual 1e-8 on the 64^3 random-moduli tet mesh, FP64
 against mixed precision (FP32 CG with FP64 dots, FP64 residual and energy),
-both with block-Jacobi PCG.
+with block-Jacobi PCG, and mixed precision with the learned block
+preconditioner (weights trained on seeds 1-16 of the same mesh family).
 `--impl reference` times the FP64 CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
@@ -45,7 +46,7 @@ WORKLOAD = "tet64"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=64, help="cells per side")
@@ -97,15 +98,14 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join("/tmp", f"fem_clocks_{os.getpid()}.csv")
+        self.lines = []
 
     def __enter__(self):
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
         time.sleep(0.3)
@@ -114,14 +114,14 @@ class ClockSampler:
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
-            self.proc.wait(timeout=10)
-            self.f.close()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = out.splitlines()
 
     def summary(self):
-        if not self.proc or not os.path.exists(self.path):
+        if not self.proc or not self.lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         rows = []
-        for line in open(self.path):
+        for line in self.lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -252,9 +252,19 @@ def newton_arms(n, n_steps, dev):
     gm = Mesh.from_fixture(m, precision="mixed")
     ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+    arms = [("fp64_block_jacobi", torch.float64, {}), ("mixed_block_jacobi", torch.float32, {})]
+    weights = os.path.join(ROOT, "paper_2602_12365_b300", "weights", "lp_tet64.npz")
+    if os.path.exists(weights):
+        from paper_2602_12365_b300.learned import LearnedPreconditioner
+        arms.append(("mixed_learned", torch.float32, {"learned": LearnedPreconditioner.load(weights)}))
     out, finals = {}, {}
-    for arm, dt in (("fp64_block_jacobi", torch.float64), ("mixed_block_jacobi", torch.float32)):
+    for arm, dt, kw in arms:
         u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device=dev)
+        # one-time setup outside the timing: the solver workspace (a step at
+        # rest returns at once) and, for the learned arm, the node graph
+        gm.newton_step(u, ubar, 0.0, 0.0, cg_dtype=dt, **kw)
+        if "learned" in kw:
+            kw["learned"].blocks(gm, u.float())
         times, newton, cg = [], [], []
         s_prev = 0.0
         for k in range(1, n_steps + 1):
@@ -263,7 +273,7 @@ def newton_arms(n, n_steps, dev):
             b = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             a.record(stream)
-            st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=dt)
+            st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=dt, **kw)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b) * 1e-3)
@@ -276,10 +286,15 @@ def newton_arms(n, n_steps, dev):
     ref = finals["fp64_block_jacobi"]
     for arm, u in finals.items():
         out[arm]["u_rel_diff_vs_fp64"] = float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref))
-    return {"workload": NEWTON_WORKLOAD, "metric": "Newton-CG s/load step at relative residual 1e-8",
-            "load_steps": list(range(1, n_steps + 1)), "arms": out,
-            "speedup_mixed_vs_fp64": out["fp64_block_jacobi"]["s_per_load_step"]
-            / out["mixed_block_jacobi"]["s_per_load_step"]}
+    res = {"workload": NEWTON_WORKLOAD, "metric": "Newton-CG s/load step at relative residual 1e-8",
+           "load_steps": list(range(1, n_steps + 1)), "arms": out}
+    t64 = out["fp64_block_jacobi"]["s_per_load_step"]
+    for arm in out:
+        if arm != "fp64_block_jacobi":
+            res[f"speedup_{arm}_vs_fp64_block_jacobi"] = t64 / out[arm]["s_per_load_step"]
+    if "mixed_learned" in out:
+        res["learned_weights"] = "paper_2602_12365_b300/weights/lp_tet64.npz (seeds 1-16, 20 load steps)"
+    return res
 
 
 def run_ours(args):
@@ -305,18 +320,30 @@ def run_ours(args):
         flush.fill_(float(k))
         return flush_rd.sum()
 
-    for k in range(max(args.warmup, 3)):  # the same work as a timed step, flush included
-        flush_l2(k)
-        gm.residual(ut, out=r)
-        gm.hvp(ut, vt, out=y)
+    def warm_up():  # the same work as a timed step, flush included
+        for k in range(max(args.warmup, 3)):
+            flush_l2(k)
+            gm.residual(ut, out=r)
+            gm.hvp(ut, vt, out=y)
+
+    warm_up()
     torch.cuda.synchronize()
     assert gm.sync_status() == 0, "device status flagged during warm-up"
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    barrier(world)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # warm up again right before the timed steps, so that the GPU is busy
+        # (clocks up) when they start rather than idle since the sampler began
+        warm_up()
+        barrier(world)
+        torch.cuda.synchronize()
         wall0 = time.perf_counter()
+        # Host head start: each step costs the host ~150 us of Python, event
+        # and launch overhead, more than the GPU's flush before the step, so
+        # the GPU would idle inside the timed intervals.  A clock-bounded
+        # delay kernel ahead of the first timed event lets the host queue all
+        # steps first; the timed intervals then hold GPU work only.
+        torch.cuda._sleep(int(2.0e9 * (0.5e-3 * args.steps + 2e-3)))
         for k in range(args.steps):
             flush_l2(k)
             ev[k][0].record(stream)
