@@ -1128,6 +1128,11 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                         lds_vec<VW, T>(myAcc, n, cur);
 #pragma unroll
                         for (int c = 0; c < D; ++c) cur[c] += fc(h, a, c);
+                        // a fresh value in the padding lane keeps the store one
+                        // 16-byte access: storing back the loaded padding lets
+                        // the compiler narrow it to 8 + 4 bytes, and a 4-byte
+                        // store at a 16-byte stride hits a bank 4 times
+                        if constexpr (VW > D) cur[VW - 1] = T(0);
                         sts_vec<VW, T>(myAcc, n, cur);
                     }
                 }
