@@ -445,6 +445,24 @@ __host__ __device__ constexpr double hex_dN(int a, int q, int j) {
 // hi + lo updated by Knuth's TwoSum, an error-free transformation, so the pair
 // holds the lane's sum to about 2^-46 relative before it is widened to double
 // once per tile; s1, a magnitude estimate, is a plain float sum.
+// (hi, lo) += x by Knuth's TwoSum (FP32, error-free)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+// warp total of (hi, lo) pairs, a fixed butterfly; every lane ends with it
+__device__ __forceinline__ void ff_warp_total(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, oh);
+        lo += ol;
+    }
+}
+
 template <typename T>
 struct ScalarAcc;
 template <>
@@ -460,13 +478,7 @@ template <>
 struct ScalarAcc<float> {
     float hi = 0.f, lo = 0.f, s1 = 0.f;
     int ninv = 0;
-    __device__ __forceinline__ void add0(float x) {
-        const float s = hi + x;
-        const float bp = s - hi;
-        const float ap = s - bp;
-        lo += (hi - ap) + (x - bp);
-        hi = s;
-    }
+    __device__ __forceinline__ void add0(float x) { ff_add(hi, lo, x); }
     __device__ __forceinline__ void add1(float x) { s1 += x; }
     __device__ __forceinline__ double total0() const { return (double)hi + (double)lo; }
     __device__ __forceinline__ double total1() const { return (double)s1; }
@@ -1171,8 +1183,25 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         }
         if (!gathered && !timed_out) gather(i + 1);  // a warp without rounds in this tile
 
-        // 4. scalar partial of this tile (fixed order)
-        if ((OP == OP_ENERGY || OP == OP_HVP) && want_scalar) {
+        // 4. scalar partial of this tile (fixed order).  The HVP's vKv: one
+        // sum, kept in FP32 pairs through the warps for FP32 calls (FP64
+        // instructions issue at a small fraction of the FP32 rate here)
+        if (OP == OP_HVP && want_scalar) {
+            if constexpr (sizeof(T) == 4) {
+                float hi = acc.hi, lo = acc.lo;
+                ff_warp_total(hi, lo);
+                if (lane == 0) {
+                    reinterpret_cast<float*>(sRed)[warp * 2 + 0] = hi;
+                    reinterpret_cast<float*>(sRed)[warp * 2 + 1] = lo;
+                }
+            } else {
+                double s0 = acc.total0();
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                if (lane == 0) sRed[warp * 4] = s0;
+            }
+        }
+        if (OP == OP_ENERGY && want_scalar) {
             double s0 = acc.total0(), s1 = acc.total1(), s2 = (double)acc.ninv;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -1187,8 +1216,25 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             }
         }
         __syncthreads();
-        if constexpr (OP == OP_ENERGY || OP == OP_HVP) {
-            if (tid == 0 && (OP == OP_ENERGY || p.out_scalar != nullptr)) {
+        if constexpr (OP == OP_HVP) {
+            if (tid == 0 && want_scalar) {
+                if constexpr (sizeof(T) == 4) {
+                    float hi = 0.f, lo = 0.f;
+                    for (int w = 0; w < kWarps; ++w) {
+                        ff_add(hi, lo, reinterpret_cast<const float*>(sRed)[w * 2 + 0]);
+                        lo += reinterpret_cast<const float*>(sRed)[w * 2 + 1];
+                    }
+                    reinterpret_cast<float*>(p.tile_red + (int64_t)t * 4)[0] = hi;
+                    reinterpret_cast<float*>(p.tile_red + (int64_t)t * 4)[1] = lo;
+                } else {
+                    double a0 = 0;
+                    for (int w = 0; w < kWarps; ++w) a0 += sRed[w * 4];
+                    p.tile_red[(int64_t)t * 4] = a0;
+                }
+            }
+        }
+        if constexpr (OP == OP_ENERGY) {
+            if (tid == 0) {
                 double a0 = 0, a1 = 0, a2 = 0;
                 for (int w = 0; w < kWarps; ++w) {
                     a0 += sRed[w * 4 + 0];
@@ -1254,6 +1300,56 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         if (lane == 0 && wf) atomicOr(sFlag, wf);
     }
 
+    // 7. the HVP's vKv: the last CTA adds the tile partials in tile order
+    // (FP32 pairs for FP32 calls, doubles for FP64 calls)
+    if (OP == OP_HVP && want_scalar) {
+        __shared__ int s_last_h;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            s_last_h = (atomicAdd(p.tile_counter, 1u) == (unsigned)G - 1u);
+        }
+        __syncthreads();
+        if (s_last_h) {
+            __threadfence();
+            if constexpr (sizeof(T) == 4) {
+                float hi = 0.f, lo = 0.f;
+                for (int t = tid; t < p.n_tiles; t += kThreads) {
+                    const float2 x = __ldcg(reinterpret_cast<const float2*>(p.tile_red + (int64_t)t * 4));
+                    ff_add(hi, lo, x.x);
+                    lo += x.y;
+                }
+                ff_warp_total(hi, lo);
+                if (lane == 0) {
+                    reinterpret_cast<float*>(sRed)[warp * 2 + 0] = hi;
+                    reinterpret_cast<float*>(sRed)[warp * 2 + 1] = lo;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    float h = 0.f, l = 0.f;
+                    for (int w = 0; w < kWarps; ++w) {
+                        ff_add(h, l, reinterpret_cast<const float*>(sRed)[w * 2 + 0]);
+                        l += reinterpret_cast<const float*>(sRed)[w * 2 + 1];
+                    }
+                    p.out_scalar[0] = (double)h + (double)l;
+                    *p.tile_counter = 0u;
+                }
+            } else {
+                double a = 0.0;
+                for (int t = tid; t < p.n_tiles; t += kThreads) a += __ldcg(p.tile_red + (int64_t)t * 4);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) sRed[warp * 4] = a;
+                __syncthreads();
+                if (tid == 0) {
+                    double h = 0.0;
+                    for (int w = 0; w < kWarps; ++w) h += sRed[w * 4];
+                    p.out_scalar[0] = h;
+                    *p.tile_counter = 0u;
+                }
+            }
+        }
+    }
     // 7. energy: the last CTA reduces the tile partials in tile order
     if constexpr (OP == OP_ENERGY) {
         __shared__ int s_last;
@@ -1281,14 +1377,13 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// finalize: each shared node's partial slots summed in slot order; nodes of
-// no element; the HVP's vKv from the tile partials
+// finalize: each shared node's partial slots summed in slot order, and nodes
+// of no element
 // ---------------------------------------------------------------------------
 template <int D, typename T, int OP>
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) {
     constexpr int VW = D == 2 ? 2 : 4;
     constexpr int AW = (OP == OP_BLOCKDIAG) ? (D == 2 ? 4 : 6) : VW;
-    __shared__ double scratch[kFinThreads / 32 * 4];
     grid_dependency_wait();  // the tile kernel's writes are visible past this point
     if (p.skip != nullptr && *p.skip != 0) return;
     const T* part = static_cast<const T*>(p.partial);
@@ -1326,11 +1421,6 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) 
         }
     }
     if (fl) atomicOr(p.status, fl);
-    if (OP == OP_HVP && p.out_scalar != nullptr && blockIdx.x == 0) {
-        double S0 = 0, S1 = 0, N = 0;
-        reduce_tiles(p.tile_red, p.n_tiles, kFinThreads, scratch, S0, S1, N);
-        if (threadIdx.x == 0) p.out_scalar[0] = S0;
-    }
 }
 
 }  // namespace fem

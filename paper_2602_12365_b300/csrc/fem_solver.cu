@@ -23,9 +23,11 @@
 // block diagonal, preconditioner and vectors -- in FP32 on an FP32 shadow of
 // u, with every dot product and norm accumulated in FP64.
 //
-// The PCG loop runs on the device: alpha, beta, the residual norm and a
-// `done` state live in device memory, every kernel of an iteration returns at
-// once when done is set, and the host enqueues iterations in batches and
+// The PCG loop runs on the device, in the Chronopoulos-Gear form (one HVP
+// with its fused z . K z and one update kernel per iteration; the iterates
+// are those of standard PCG): alpha, beta, the residual norm and a `done`
+// state live in device memory, every kernel of an iteration returns at once
+// when done is set, and the host enqueues iterations in batches and
 // reads done one batch behind, so the GPU never waits for the host inside a
 // solve.  Every reduction is a fixed-order FP64 sum (per-thread strided
 // sums, a warp butterfly, warps in order, blocks in order by the last block),
@@ -48,16 +50,17 @@ constexpr int kVT = 256;          // threads of the vector kernels
 constexpr int kMaxRedBlocks = 1184;  // partial-sum slots (8 blocks per SM on 148 SMs)
 constexpr int kVecBlocks = 592;      // grid of the vector kernels: 4 blocks per SM
 
-// device-resident scalars of one PCG solve
+// device-resident scalars of one PCG solve (Chronopoulos-Gear form)
 struct CgState {
-    double rz;    // res . z
-    double pq;    // p . K p (written by the HVP's fused reduction)
-    double rr;    // res . res
-    double tol;   // absolute tolerance on ||res||
-    double beta;
+    double gamma;      // r . z
+    double delta;      // z . K z (written by the HVP's fused reduction)
+    double rr;         // r . r
+    double tol;        // absolute tolerance on ||r||
+    double gamma_old;  // r . z of the previous iteration
+    double alpha;      // step of the previous iteration
     long long cg_max;
-    int done;     // 0 running, 1 converged, 2 non-positive curvature, 3 iteration cap
-    int k;        // iterations (HVPs) performed
+    int done;  // 0 running, 1 converged, 2 non-positive curvature, 3 iteration cap
+    int k;     // iterations (HVPs) performed
     unsigned counter;  // last-block arrival counter
     int pad;
 };
@@ -200,56 +203,54 @@ __device__ __forceinline__ void apply_block(const T* Minv, int64_t n, const T (&
 // ---------------------------------------------------------------------------
 // PCG kernels (one node per thread, grid-stride)
 // ---------------------------------------------------------------------------
+// PCG in the Chronopoulos-Gear form: the iterates of the standard
+// preconditioned CG (x_k, r_k, p_k, one HVP per iteration, the same stop and
+// non-positive-curvature rules), with s = K p carried by recurrence so that an
+// iteration needs one HVP, w = K z (its z . K z fused into the HVP), and one
+// update kernel whose last block forms r . r and r . z:
+//   beta = gamma / gamma_old, p^T K p = delta - beta gamma / alpha_old,
+//   alpha = gamma / p^T K p, p = z + beta p, s = w + beta s,
+//   x += alpha p, r -= alpha s, z = M r.
 template <int D, typename T>
-__global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* res, T* z, T* p,
+__global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* r, T* z, T* p, T* s,
                                                const T* Minv, CgState* st, double* partial) {
     typename AccT<T>::type v[2] = {};
     for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
-        T r[3] = {0, 0, 0}, zz[3];
+        T rv[3] = {0, 0, 0}, zz[3];
 #pragma unroll
-        for (int c = 0; c < D; ++c) r[c] = b[n * D + c];
-        apply_block<D, T>(Minv, n, r, zz);
+        for (int c = 0; c < D; ++c) rv[c] = b[n * D + c];
+        apply_block<D, T>(Minv, n, rv, zz);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             x[n * D + c] = T(0);
-            res[n * D + c] = r[c];
+            r[n * D + c] = rv[c];
             z[n * D + c] = zz[c];
-            p[n * D + c] = zz[c];
-            acc_prod(v[0], r[c], r[c]);
-            acc_prod(v[1], r[c], zz[c]);
+            p[n * D + c] = T(0);
+            s[n * D + c] = T(0);
+            acc_prod(v[0], rv[c], rv[c]);
+            acc_prod(v[1], rv[c], zz[c]);
         }
     }
     double tot[2];
     if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
         st->rr = tot[0];
-        st->rz = tot[1];
+        st->gamma = tot[1];
         st->k = 0;
         st->done = (sqrt(tot[0]) <= st->tol) ? 1 : 0;
     }
 }
 
-// pq = p . q for the step length (a separate pass: p and q are still in L2)
 template <int D, typename T>
-__global__ void __launch_bounds__(kVT) cg_pq(int64_t nn, const T* p, const T* q, CgState* st, double* partial) {
+__global__ void __launch_bounds__(kVT) cg_step(int64_t nn, T* x, T* r, T* z, T* p, T* s, const T* w,
+                                               const T* Minv, CgState* st, double* partial) {
     if (st->done) return;  // uniform: only the last block of a kernel writes done
-    typename AccT<T>::type v[1] = {};
-    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < nn * D; i += (int64_t)gridDim.x * kVT)
-        acc_prod(v[0], p[i], q[i]);
-    double tot[1];
-    if (grid_total<1>(v, tot, partial, &st->counter) && threadIdx.x == 0) st->pq = tot[0];
-}
-
-// alpha = rz / pq; x += alpha p; res -= alpha q; z = Minv res; new rz, rr;
-// convergence test and beta by the last block
-template <int D, typename T>
-__global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z, const T* p, const T* q,
-                                                 const T* Minv, CgState* st, double* partial) {
-    if (st->done) return;
-    const double pq = st->pq, rz = st->rz;
+    const double gamma = st->gamma, delta = st->delta;
     const int k = st->k;
+    const double beta = k == 0 ? 0.0 : gamma / st->gamma_old;
+    const double pKp = k == 0 ? delta : delta - beta * gamma / st->alpha;
     typename AccT<T>::type v[2] = {};
     double tot[2];
-    if (!(pq > 0.0)) {
+    if (!(pKp > 0.0)) {
         // non-positive curvature: stop; at the first iteration take d = P r
         if (k == 0)
             for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT)
@@ -261,21 +262,27 @@ __global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z,
         }
         return;
     }
-    const T alpha = (T)(rz / pq);
+    const double alpha = gamma / pKp;
+    const T a = (T)alpha, bt = (T)beta;
     for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
-        T r[3] = {0, 0, 0}, zz[3];
+        T rv[3] = {0, 0, 0}, zz[3];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            x[n * D + c] += alpha * p[n * D + c];
-            r[c] = res[n * D + c] - alpha * q[n * D + c];
-            res[n * D + c] = r[c];
+            const int64_t i = n * D + c;
+            const T pn = z[i] + bt * p[i];
+            const T sn = w[i] + bt * s[i];
+            p[i] = pn;
+            s[i] = sn;
+            x[i] += a * pn;
+            rv[c] = r[i] - a * sn;
+            r[i] = rv[c];
         }
-        apply_block<D, T>(Minv, n, r, zz);
+        apply_block<D, T>(Minv, n, rv, zz);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             z[n * D + c] = zz[c];
-            acc_prod(v[0], r[c], r[c]);
-            acc_prod(v[1], r[c], zz[c]);
+            acc_prod(v[0], rv[c], rv[c]);
+            acc_prod(v[1], rv[c], zz[c]);
         }
     }
     if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
@@ -285,19 +292,12 @@ __global__ void __launch_bounds__(kVT) cg_update(int64_t nn, T* x, T* res, T* z,
         if (sqrt(tot[0]) <= st->tol) {
             st->done = 1;
         } else {
-            st->beta = tot[1] / rz;
-            st->rz = tot[1];
+            st->gamma_old = gamma;
+            st->gamma = tot[1];
+            st->alpha = alpha;
             if (k1 >= st->cg_max) st->done = 3;
         }
     }
-}
-
-template <int D, typename T>
-__global__ void __launch_bounds__(kVT) cg_pupdate(int64_t nn, T* p, const T* z, const CgState* st) {
-    if (st->done) return;
-    const T beta = (T)st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < nn * D; i += (int64_t)gridDim.x * kVT)
-        p[i] = z[i] + beta * p[i];
 }
 
 // FP64 dot product a . b with a fixed summation order
@@ -467,7 +467,7 @@ struct SolverWork {
     std::vector<double*> saves;  // one per bisection depth
     float *u32 = nullptr, *du32 = nullptr;
     // CG vectors, index 0: FP64, 1: FP32 (allocated on first use)
-    void *b[2] = {}, *x[2] = {}, *res[2] = {}, *z[2] = {}, *p[2] = {}, *q[2] = {}, *Minv[2] = {},
+    void *b[2] = {}, *x[2] = {}, *res[2] = {}, *z[2] = {}, *p[2] = {}, *q[2] = {}, *s[2] = {}, *Minv[2] = {},
          *Db[2] = {};
     double* partial = nullptr;
     CgState* cg = nullptr;
@@ -541,7 +541,7 @@ fem_status ensure_work(fem_mesh* m, int cg_dtype) {
     const int pi = cg_dtype == FEM_F64 ? 0 : 1;
     if (!w->b[pi]) {
         const size_t ts = pi == 0 ? 8 : 4;
-        void** vecs[] = {&w->b[pi], &w->x[pi], &w->res[pi], &w->z[pi], &w->p[pi], &w->q[pi]};
+        void** vecs[] = {&w->b[pi], &w->x[pi], &w->res[pi], &w->z[pi], &w->p[pi], &w->q[pi], &w->s[pi]};
         for (void** v : vecs) {
             uint8_t* q = nullptr;
             FEM_TRY(dalloc(w, &q, (size_t)w->nd * ts));
@@ -732,13 +732,12 @@ private:
     fem_status launch_cg_iteration(const void* ucg) {
         SolverWork* w = w_;
         const int pi = pi_;
-        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->p[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
+        // w = K z with z . K z (fused), then the update
+        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], &w->cg->delta, FEM_MASK_IN | FEM_MASK_OUT,
                              st_, &w->cg->done));
-        cg_pq<D, T><<<grid_dofs(), kVT, 0, st_>>>(w->nn, (const T*)w->p[pi], (const T*)w->q[pi], w->cg, w->partial);
-        cg_update<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
-                                                      (const T*)w->p[pi], (const T*)w->q[pi],
-                                                      (const T*)w->Minv[pi], w->cg, w->partial);
-        cg_pupdate<D, T><<<grid_dofs(), kVT, 0, st_>>>(w->nn, (T*)w->p[pi], (const T*)w->z[pi], w->cg);
+        cg_step<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
+                                                    (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
+                                                    (const T*)w->Minv[pi], w->cg, w->partial);
         CUDA_TRY(cudaGetLastError());
         return FEM_OK;
     }
@@ -756,8 +755,8 @@ private:
         CUDA_TRY(cudaMemcpyAsync(&w->cg->tol, &h->cg.tol, sizeof(double), cudaMemcpyHostToDevice, st_));
         CUDA_TRY(cudaMemcpyAsync(&w->cg->cg_max, &h->cg.cg_max, sizeof(long long), cudaMemcpyHostToDevice, st_));
         cg_init<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],
-                                                    (T*)w->z[pi], (T*)w->p[pi], (const T*)w->Minv[pi], w->cg,
-                                                    w->partial);
+                                                    (T*)w->z[pi], (T*)w->p[pi], (T*)w->s[pi], (const T*)w->Minv[pi],
+                                                    w->cg, w->partial);
         CUDA_TRY(cudaGetLastError());
         const int B = o_.cg_batch > 0 ? o_.cg_batch : 8;
         const int64_t max_batches = cg_max_ / B + 3;
