@@ -325,7 +325,8 @@ fem_status static_scratch(ReductionScratch* out) {
 
 fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
                   double* out_scalar, double* out_mu, double* out_lam, unsigned flags,
-                  cudaStream_t st, const ReductionScratch* scratch = nullptr, const int* skip = nullptr) {
+                  cudaStream_t st, const ReductionScratch* scratch = nullptr, const int* skip = nullptr,
+                  int vkv_tiles = 0) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
     if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
@@ -362,6 +363,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.tile_counter = scratch ? scratch->counter : m->tile_counter;
     p.status = m->status;
     p.skip = skip;
+    p.vkv_tiles = vkv_tiles;
     p.u = u;
     p.v = v;
     p.out = out;
@@ -463,9 +465,11 @@ namespace femi {
 fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
 
 fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
-                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip) {
-    return launch(m, dtype, op, u, v, out, out_scalar, nullptr, nullptr, flags, st, nullptr, skip);
+                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip, int vkv_tiles) {
+    return launch(m, dtype, op, u, v, out, out_scalar, nullptr, nullptr, flags, st, nullptr, skip, vkv_tiles);
 }
+
+const double* tile_partials(const fem_mesh* m) { return m->tile_red; }
 }  // namespace femi
 
 extern "C" {

@@ -177,6 +177,7 @@ struct KParams {
     unsigned* tile_counter;
     int* status;
     const int* skip;  // device flag: the call does nothing when *skip != 0 (may be null)
+    int vkv_tiles;    // HVP: write the per-tile vKv partials (tile_red) even without out_scalar
     // call
     const void* u;
     const void* v;
@@ -956,7 +957,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const T* gx = static_cast<const T*>(p.X);
     const T mu0 = (T)p.mu0, lam0 = (T)p.lam0;
     // the HVP's fused vKv only when the caller asked for it
-    const bool want_scalar = (OP == OP_ENERGY) || (OP == OP_HVP && p.out_scalar != nullptr);
+    const bool want_scalar = (OP == OP_ENERGY) || (OP == OP_HVP && (p.out_scalar != nullptr || p.vkv_tiles));
     int flags_local = 0;
 
     // 0. tile table and barriers
@@ -1302,7 +1303,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
 
     // 7. the HVP's vKv: the last CTA adds the tile partials in tile order
     // (FP32 pairs for FP32 calls, doubles for FP64 calls)
-    if (OP == OP_HVP && want_scalar) {
+    if (OP == OP_HVP && p.out_scalar != nullptr) {
         __shared__ int s_last_h;
         __syncthreads();
         if (tid == 0) {

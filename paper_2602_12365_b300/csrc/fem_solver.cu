@@ -53,7 +53,7 @@ constexpr int kVecBlocks = 592;      // grid of the vector kernels: 4 blocks per
 // device-resident scalars of one PCG solve (Chronopoulos-Gear form)
 struct CgState {
     double gamma;      // r . z
-    double delta;      // z . K z (written by the HVP's fused reduction)
+    double delta;      // unused (z . K z is reduced from the HVP's tile partials)
     double rr;         // r . r
     double tol;        // absolute tolerance on ||r||
     double gamma_old;  // r . z of the previous iteration
@@ -240,11 +240,41 @@ __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* 
     }
 }
 
+// z . K z from the HVP's per-tile partials, summed by every block in the same
+// fixed order (so every block holds the same value without a grid-wide wait)
+template <typename T>
+__device__ __forceinline__ double tile_total(const double* tile_red, int n_tiles) {
+    __shared__ double sh[kVT / 32];
+    __shared__ double tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    typename AccT<T>::type a{};
+    for (int t = threadIdx.x; t < n_tiles; t += kVT) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 x = __ldcg(reinterpret_cast<const float2*>(tile_red + (int64_t)t * 4));
+            ff_add(a, x.x);
+            a.lo += x.y;
+        } else {
+            a += __ldcg(tile_red + (int64_t)t * 4);
+        }
+    }
+    const double v = warp_total(a);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kVT / 32; ++w) s += sh[w];
+        tot = s;
+    }
+    __syncthreads();
+    return tot;
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(kVT) cg_step(int64_t nn, T* x, T* r, T* z, T* p, T* s, const T* w,
-                                               const T* Minv, CgState* st, double* partial) {
+                                               const T* Minv, CgState* st, double* partial,
+                                               const double* tile_red, int n_tiles) {
     if (st->done) return;  // uniform: only the last block of a kernel writes done
-    const double gamma = st->gamma, delta = st->delta;
+    const double gamma = st->gamma, delta = tile_total<T>(tile_red, n_tiles);
     const int k = st->k;
     const double beta = k == 0 ? 0.0 : gamma / st->gamma_old;
     const double pKp = k == 0 ? delta : delta - beta * gamma / st->alpha;
@@ -733,11 +763,12 @@ private:
         SolverWork* w = w_;
         const int pi = pi_;
         // w = K z with z . K z (fused), then the update
-        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], &w->cg->delta, FEM_MASK_IN | FEM_MASK_OUT,
-                             st_, &w->cg->done));
+        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
+                             st_, &w->cg->done, /*vkv_tiles=*/1));
         cg_step<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
                                                     (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
-                                                    (const T*)w->Minv[pi], w->cg, w->partial);
+                                                    (const T*)w->Minv[pi], w->cg, w->partial,
+                                                    femi::tile_partials(m_), m_->info.n_tiles);
         CUDA_TRY(cudaGetLastError());
         return FEM_OK;
     }
