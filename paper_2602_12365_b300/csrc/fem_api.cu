@@ -16,7 +16,6 @@
 #include "fem_plan.h"
 
 static_assert(fem::kEmptyLane == fem::kNoNode, "kernel and planner agree on empty lanes");
-static_assert(fem::kNodeAlign % 16 == 0, "tile node lists must be bulk-copyable");
 
 namespace {
 thread_local std::string g_err;

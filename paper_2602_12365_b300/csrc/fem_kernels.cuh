@@ -91,10 +91,10 @@ __host__ __device__ constexpr int rounds_per_iter(int et, int tsize, int op) {
 // partial slots, Dirichlet bits), the per-warp accumulator copies, reduction
 // scratch, the CTA's tile table, the per-warp record ring and the mbarriers.
 // ---------------------------------------------------------------------------
-constexpr int kMaxTilesPerCta = 64;
+constexpr int kMaxTilesPerCta = 16;
 
 struct SmemLayout {
-    int off_u, off_v, off_x, off_gid, off_slot, off_mask, buf_bytes;  // inside one node buffer
+    int off_u, off_v, off_x, buf_bytes;  // inside one node buffer
     int off_buf0, off_buf1, off_acc, acc_bytes, off_red, off_tab, off_ring, off_bar, total, aw,
         stage_bytes;
 };
@@ -118,12 +118,6 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     if (need_v) o = align16(o + nlp * vec);
     L.off_x = o;
     if (et == 2) o = align16(o + nlp * vec);
-    L.off_gid = o;
-    o = align16(o + nlp * 4);
-    L.off_slot = o;
-    o = align16(o + nlp * 4);
-    L.off_mask = o;
-    o = align16(o + nlp);
     L.buf_bytes = align128(o);
     L.off_buf0 = 0;
     L.off_buf1 = L.buf_bytes;
@@ -139,7 +133,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
     L.off_bar = o = align16(o);
-    o += (kWarps * kStages + 2) * 8;
+    o += kWarps * kStages * 8;
     L.total = align16(o);
     return L;
 }
@@ -949,7 +943,6 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     int4* tab = reinterpret_cast<int4*>(smem + L.off_tab);  // (node begin, padded count, round begin, rounds)
     uint8_t* ring = smem + L.off_ring + warp * kStages * L.stage_bytes;
     uint64_t* rbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp * kStages;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + kWarps * kStages;  // [2]
     auto buf = [&](int b) { return smem + (b ? L.off_buf1 : L.off_buf0); };
 
     const T* gu = static_cast<const T*>(p.u);
@@ -968,46 +961,57 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         tab[i] = make_int4((int)n0, (int)(n1 - n0), r0, r1 - r0);
     }
     if (tid == 0) {
-        for (int k = 0; k < kWarps * kStages + 2; ++k)
+        for (int k = 0; k < kWarps * kStages; ++k)
             mbar_init(reinterpret_cast<uint64_t*>(smem + L.off_bar) + k, 1);
         *sFlag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    // node ids / slots / Dirichlet bits of tile i into buffer i & 1 (one thread)
-    auto issue_meta = [&](int i) {
+    // Node metadata (global id, partial slot, Dirichlet bits) of the current
+    // and the next tile, in registers: node j = tid + kThreads k for k < kMeta
+    // (nodes of larger tiles beyond that are read from global memory where
+    // used).  The next tile's metadata is loaded a tile ahead of its use.
+    constexpr int kMeta = (ET == 2) ? 1 : 4;
+    struct Meta {
+        int g[kMeta], s[kMeta];
+        uint32_t m;
+    };
+    auto load_meta = [&](int i, Meta& M) {
         const int4 tb = tab[i];
-        unsigned char* B = buf(i & 1);
-        uint64_t* bar = &mbar[i & 1];
-        mbar_arrive_expect_tx(bar, (uint32_t)(tb.y * 9));
-        bulk_copy(B + L.off_gid, p.node_gid + tb.x, (uint32_t)(tb.y * 4), bar);
-        bulk_copy(B + L.off_slot, p.node_slot + tb.x, (uint32_t)(tb.y * 4), bar);
-        bulk_copy(B + L.off_mask, p.node_mask_local + tb.x, (uint32_t)tb.y, bar);
+        M.m = 0u;
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k) {
+            const int j = tid + kThreads * k;
+            M.g[k] = -1;
+            M.s[k] = -1;
+            if (j < tb.y) {
+                M.g[k] = __ldg(p.node_gid + tb.x + j);
+                M.s[k] = __ldg(p.node_slot + tb.x + j);
+                M.m |= (uint32_t)__ldg(p.node_mask_local + tb.x + j) << (8 * k);
+            }
+        }
     };
     // gather tile i's nodal values into buffer i & 1 (all threads, cp.async)
-    auto gather = [&](int i) {
-        const int b = i & 1;
-        if (!mbar_wait_bounded(&mbar[b], (uint32_t)((i >> 1) & 1))) {
-            flags_local |= 4;
-            return;
-        }
-        unsigned char* B = buf(b);
-        const int32_t* bgid = reinterpret_cast<const int32_t*>(B + L.off_gid);
+    auto gather = [&](int i, const Meta& M) {
+        const int4 tb = tab[i];
+        unsigned char* B = buf(i & 1);
         T* bu = reinterpret_cast<T*>(B + L.off_u);
         T* bv = reinterpret_cast<T*>(B + L.off_v);
         T* bx = reinterpret_cast<T*>(B + L.off_x);
-        const int nlp = tab[i].y;
-        for (int j = tid; j < nlp; j += kThreads) {
-            const int64_t g = bgid[j];
-            if (g < 0) continue;
+        auto one = [&](int j, int64_t g) {
+            if (g < 0) return;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 cp_async<sizeof(T)>(bu + j * VW + c, gu + g * D + c);
                 if constexpr (kNeedV) cp_async<sizeof(T)>(bv + j * VW + c, gv + g * D + c);
                 if constexpr (ET == 2) cp_async<sizeof(T)>(bx + j * VW + c, gx + g * D + c);
             }
-        }
+        };
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k)
+            if (tid + kThreads * k < tb.y) one(tid + kThreads * k, M.g[k]);
+        for (int j = tid + kThreads * kMeta; j < tb.y; j += kThreads) one(j, __ldg(p.node_gid + tb.x + j));
         cp_async_commit();
     };
 
@@ -1036,13 +1040,12 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     };
 
     // 1. start: metadata of the first two tiles, the ring, tile 0's gathers
-    if (tid == 0) {
-        issue_meta(0);
-        if (n_my > 1) issue_meta(1);
-    }
+    Meta cur, nxt;
+    load_meta(0, cur);
+    if (n_my > 1) load_meta(1, nxt);
     if (lane == 0)
         for (int k = 0; k < kStages; ++k) issue_next();
-    gather(0);
+    gather(0, cur);
 
     int consumed = 0, c_slot = 0;
     uint32_t c_phase = 0;
@@ -1054,17 +1057,14 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         T* sU = reinterpret_cast<T*>(B + L.off_u);
         T* sV = reinterpret_cast<T*>(B + L.off_v);
         T* sX = reinterpret_cast<T*>(B + L.off_x);
-        const int32_t* sGid = reinterpret_cast<const int32_t*>(B + L.off_gid);
-        const int32_t* sSlot = reinterpret_cast<const int32_t*>(B + L.off_slot);
-        const uint8_t* sMask = B + L.off_mask;
         const int nlp = tab[i].y;
+        const int64_t nbase = tab[i].x;
 
         cp_async_wait_all();
         __syncthreads();
         // 2. fix-ups of the gathered values; zero the accumulators
-        for (int j = tid; j < nlp; j += kThreads) {
-            if (sGid[j] < 0) continue;
-            const uint8_t m = sMask[j];
+        auto fixup = [&](int j, int g, uint32_t m) {
+            if (g < 0) return;
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -1075,7 +1075,12 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                 }
             }
             if (!fin) flags_local |= 2;
-        }
+        };
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k)
+            if (tid + kThreads * k < nlp) fixup(tid + kThreads * k, cur.g[k], (cur.m >> (8 * k)) & 0xffu);
+        for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
+            fixup(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_mask_local + nbase + j));
         if constexpr (kNeedAcc) {
             int4* z = reinterpret_cast<int4*>(sAcc);
             const int nz = align16(kWarps * nlp * AW * (int)sizeof(T)) / 16;
@@ -1116,7 +1121,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                 issue_next();
             }
             if (!gathered) {  // the next tile's nodes, spread over all threads
-                gather(i + 1);
+                gather(i + 1, nxt);
                 gathered = true;
             }
             // element contributions: f[h] for round k0 + h (scalar), or both
@@ -1182,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             }
             __syncwarp();
         }
-        if (!gathered && !timed_out) gather(i + 1);  // a warp without rounds in this tile
+        if (!gathered && !timed_out) gather(i + 1, nxt);  // a warp without rounds in this tile
 
         // 4. scalar partial of this tile (fixed order).  The HVP's vKv: one
         // sum, kept in FP32 pairs through the warps for FP32 calls (FP64
@@ -1252,9 +1257,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         if constexpr (kNeedAcc) {
             T* part = static_cast<T*>(p.partial);
             T* out = static_cast<T*>(p.out);
-            for (int j = tid; j < nlp; j += kThreads) {
-                const int g = sGid[j];
-                if (g < 0) continue;
+            auto combine = [&](int j, int g, int slot, uint32_t msk) {
+                if (g < 0) return;
                 T sum[6] = {0, 0, 0, 0, 0, 0};
                 if constexpr (OP == OP_BLOCKDIAG) {
 #pragma unroll
@@ -1269,25 +1273,29 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                         for (int c = 0; c < VW; ++c) sum[c] += tv[c];
                     }
                 }
-                const int slot = sSlot[j];
                 if (slot < 0) {
                     if constexpr (OP == OP_BLOCKDIAG)
-                        flags_local |= write_block<D, T>(out, g, sum, sMask[j]);
+                        flags_local |= write_block<D, T>(out, g, sum, (uint8_t)msk);
                     else
-                        flags_local |= write_vec<D, T>(out, g, sum, sMask[j], p.flags);
+                        flags_local |= write_vec<D, T>(out, g, sum, (uint8_t)msk, p.flags);
                 } else if constexpr (OP == OP_BLOCKDIAG) {
                     for (int c = 0; c < AW; ++c) part[(int64_t)slot * AW + c] = sum[c];
                 } else {
                     sts_vec<VW, T>(part, slot, sum);  // one node vector per slot
                 }
-            }
+            };
+#pragma unroll
+            for (int k = 0; k < kMeta; ++k)
+                if (tid + kThreads * k < nlp)
+                    combine(tid + kThreads * k, cur.g[k], cur.s[k], (cur.m >> (8 * k)) & 0xffu);
+            for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
+                combine(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_slot + nbase + j),
+                        __ldg(p.node_mask_local + nbase + j));
         }
         __syncthreads();
-        // 6. buffer i & 1 is free: bring in the metadata of tile i + 2
-        if (tid == 0 && i + 2 < n_my) {
-            fence_proxy_async_smem();
-            issue_meta(i + 2);
-        }
+        // 6. the next tile's metadata becomes current; load tile i + 2's
+        cur = nxt;
+        if (i + 2 < n_my) load_meta(i + 2, nxt);
     }
     if (timed_out) flags_local |= 4;
     // drain the copies still in flight before the CTA may exit
