@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=64, help="cells per side")
+    ap.add_argument("--cells", dest="n", type=int, default=64, help="cells per side of the tet workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--newton-steps", type=int, default=2,
@@ -432,7 +432,7 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
-    if args.newton_steps > 0:
+    if args.newton_steps > 0 and rank == 0:  # a per-GPU measurement, reported by rank 0
         line["newton"] = newton_arms(args.n, args.newton_steps, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, t = cpu_oracle_rate(m, u, v)
