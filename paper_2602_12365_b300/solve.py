@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--of", type=int, default=20, help="load steps of the whole path")
     ap.add_argument("--cg", default="f32", choices=["f32", "f64"])
     ap.add_argument("--learned", default=None, help="weights (.npz) of the learned preconditioner")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="then the compliance and its gradient in the per-element mu (lambda = 10 mu)")
     a = ap.parse_args()
     seed = a.seed if a.seed is not None else (a.moduli if a.moduli is not None else 0)
     if a.workload == "tri":
@@ -55,6 +57,14 @@ def main():
         print(f"step {k}/{a.of} s={s:.4f}: {time.perf_counter() - t0:.3f} s, newton {st['newton_iters']}, "
               f"cg {st['cg_iters']}, |r| {st['r_norm']:.3e} / r0 {st['r0_norm']:.3e}", flush=True)
         s_prev = s
+    if a.adjoint:
+        from .adjoint import compliance_gradient
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c, g, iters = compliance_gradient(gm, u, rtol=1e-8, cg_dtype=dt, vjp_dtype=dt)
+        torch.cuda.synchronize()
+        print(f"adjoint: {time.perf_counter() - t0:.3f} s, c = {c:.6e}, |dc/dmu| = {torch.linalg.norm(g).item():.6e}, "
+              f"cg {iters}", flush=True)
 
 
 if __name__ == "__main__":
