@@ -52,17 +52,13 @@ constexpr int kVecBlocks = 592;      // grid of the vector kernels: 4 blocks per
 
 // device-resident scalars of one PCG solve (Chronopoulos-Gear form)
 struct CgState {
-    double gamma;      // r . z
-    double delta;      // unused (z . K z is reduced from the HVP's tile partials)
-    double rr;         // r . r
-    double tol;        // absolute tolerance on ||r||
-    double gamma_old;  // r . z of the previous iteration
-    double alpha;      // step of the previous iteration
+    double rgamma[2];  // 1 / (r . z) of launch k in slot k & 1 (read by launch k + 1)
+    double pkp[2];     // p^T K p of launch k in slot k & 1
+    double rr;         // r . r at the stop
+    double tol2;       // squared absolute tolerance on ||r||
     long long cg_max;
     int done;  // 0 running, 1 converged, 2 non-positive curvature, 3 iteration cap
-    int k;     // iterations (HVPs) performed
-    unsigned counter;  // last-block arrival counter
-    int pad;
+    int k;     // iterations (HVPs) performed, set at the stop
 };
 
 struct DotState {
@@ -106,13 +102,14 @@ struct AccT<float> {
     using type = FF;
 };
 
-// warp butterfly on the accumulator, widened to double (all lanes)
-__device__ __forceinline__ double warp_total(double v) {
+// warp butterfly on the accumulator (all lanes end with the warp's sum);
+// FP32 pairs stay pairs, widened to double by the one lane that stores them
+__device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_total(FF v) {
+__device__ __forceinline__ FF warp_sum(FF v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
@@ -120,8 +117,10 @@ __device__ __forceinline__ double warp_total(FF v) {
         ff_add(v, oh);
         v.lo += ol;
     }
-    return (double)v.hi + (double)v.lo;
+    return v;
 }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(FF v) { return (double)v.hi + (double)v.lo; }
 
 // ---------------------------------------------------------------------------
 // fixed-order block reduction of NV doubles; the total lands in thread 0
@@ -154,10 +153,10 @@ __device__ __forceinline__ bool grid_total(A (&a)[NV], double (&out)[NV], double
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_total(a[k]);
+    for (int k = 0; k < NV; ++k) a[k] = warp_sum(a[k]);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k];
+        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = v[k] = widen(a[k]);
     __syncthreads();
     if (threadIdx.x == 0)
         for (int w = 1; w < kVT / 32; ++w)
@@ -200,21 +199,104 @@ __device__ __forceinline__ void apply_block(const T* Minv, int64_t n, const T (&
     }
 }
 
+// 16-byte vector access to E contiguous values (E * sizeof(T) a multiple of
+// 16, the address 16-byte aligned)
+template <typename T, int E>
+__device__ __forceinline__ void ld16(const T* src, T (&v)[E]) {
+    static_assert((E * sizeof(T)) % 16 == 0, "whole 16-byte chunks");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < E / 4; ++k) {
+            const float4 q = reinterpret_cast<const float4*>(src)[k];
+            v[4 * k] = q.x, v[4 * k + 1] = q.y, v[4 * k + 2] = q.z, v[4 * k + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) {
+            const double2 q = reinterpret_cast<const double2*>(src)[k];
+            v[2 * k] = q.x, v[2 * k + 1] = q.y;
+        }
+    }
+}
+template <typename T, int E>
+__device__ __forceinline__ void st16(T* dst, const T (&v)[E]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < E / 4; ++k)
+            reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+// nodes per group so that a group's values of one vector are whole 16-byte
+// chunks (3D FP32: 4 nodes = 48 bytes)
+__host__ __device__ constexpr int node_group(int D, int tsize) {
+    return (D * tsize) % 16 == 0 ? 1 : ((D * tsize) % 8 == 0 ? 2 : 4);
+}
+
 // ---------------------------------------------------------------------------
-// PCG kernels (one node per thread, grid-stride)
+// PCG kernels
 // ---------------------------------------------------------------------------
 // PCG in the Chronopoulos-Gear form: the iterates of the standard
 // preconditioned CG (x_k, r_k, p_k, one HVP per iteration, the same stop and
 // non-positive-curvature rules), with s = K p carried by recurrence so that an
 // iteration needs one HVP, w = K z (its z . K z fused into the HVP), and one
-// update kernel whose last block forms r . r and r . z:
+// update kernel:
 //   beta = gamma / gamma_old, p^T K p = delta - beta gamma / alpha_old,
 //   alpha = gamma / p^T K p, p = z + beta p, s = w + beta s,
 //   x += alpha p, r -= alpha s, z = M r.
+// No kernel waits for a grid-wide sum.  Each update kernel leaves per-block
+// partial sums of r . r and r . z (slot (k + 1) & 1 of the partial buffer);
+// the next one (launch k + 1, after the HVP) has every block add those and
+// the HVP's per-tile z . K z partials in the same fixed order, so every
+// block holds the same gamma, delta and ||r|| and takes the same decision:
+// stop (converged, iteration cap, non-positive curvature) or update.  The
+// stop is therefore seen one launch after the update that reached it, and
+// that launch's HVP is the only work spent past the stop.  cg_init and every
+// cg_step of one solve run on the same grid (the partial count).
+
+// accumulator + accumulator (pair or double)
+__device__ __forceinline__ void acc_add(FF& s, FF x) {
+    ff_add(s, x.hi);
+    s.lo += x.lo;
+}
+__device__ __forceinline__ void acc_add(double& s, double x) { s += x; }
+// L2 load of an accumulator another kernel wrote
+__device__ __forceinline__ FF ld_acc(const FF* q) {
+    const float2 x = __ldcg(reinterpret_cast<const float2*>(q));
+    FF f;
+    f.hi = x.x;
+    f.lo = x.y;
+    return f;
+}
+__device__ __forceinline__ double ld_acc(const double* q) { return __ldcg(q); }
+
+// fixed-order block sum of NV accumulators; the totals land in thread 0
+template <int NV, typename A>
+__device__ __forceinline__ void block_sum(A (&a)[NV], A* sh /* [kVT / 32 * NV] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] = warp_sum(a[k]);
+    __syncthreads();  // sh may hold an earlier sum
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp * NV + k] = a[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kVT / 32; ++w)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc_add(a[k], sh[w * NV + k]);
+}
+
+// r = b, z = M b, x = p = s = 0; per-block r . r and r . z into slot 0
 template <int D, typename T>
 __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* r, T* z, T* p, T* s,
-                                               const T* Minv, CgState* st, double* partial) {
-    typename AccT<T>::type v[2] = {};
+                                               const T* Minv, CgState* st,
+                                               typename AccT<T>::type* partial) {
+    using A = typename AccT<T>::type;
+    __shared__ A sh[kVT / 32 * 2];
+    A v[2] = {};
     for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
         T rv[3] = {0, 0, 0}, zz[3];
 #pragma unroll
@@ -231,70 +313,167 @@ __global__ void __launch_bounds__(kVT) cg_init(int64_t nn, const T* b, T* x, T* 
             acc_prod(v[1], rv[c], zz[c]);
         }
     }
-    double tot[2];
-    if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->gamma = tot[1];
-        st->k = 0;
-        st->done = (sqrt(tot[0]) <= st->tol) ? 1 : 0;
-    }
-}
-
-// z . K z from the HVP's per-tile partials, summed by every block in the same
-// fixed order (so every block holds the same value without a grid-wide wait)
-template <typename T>
-__device__ __forceinline__ double tile_total(const double* tile_red, int n_tiles) {
-    __shared__ double sh[kVT / 32];
-    __shared__ double tot;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    typename AccT<T>::type a{};
-    for (int t = threadIdx.x; t < n_tiles; t += kVT) {
-        if constexpr (sizeof(T) == 4) {
-            const float2 x = __ldcg(reinterpret_cast<const float2*>(tile_red + (int64_t)t * 4));
-            ff_add(a, x.x);
-            a.lo += x.y;
-        } else {
-            a += __ldcg(tile_red + (int64_t)t * 4);
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = v[0];
+        partial[2 * blockIdx.x + 1] = v[1];
+        if (blockIdx.x == 0) {
+            st->done = 0;
+            st->k = 0;
         }
     }
-    const double v = warp_total(a);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kVT / 32; ++w) s += sh[w];
-        tot = s;
-    }
-    __syncthreads();
-    return tot;
 }
 
+// one partial of z . K z per HVP tile (an FP32 pair, or a double)
+template <typename T>
+__device__ __forceinline__ typename AccT<T>::type tile_partial(const double* tile_red, int t) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 x = __ldcg(reinterpret_cast<const float2*>(tile_red + (int64_t)t * 4));
+        FF f;
+        f.hi = x.x;
+        f.lo = x.y;
+        return f;
+    } else {
+        return __ldcg(tile_red + (int64_t)t * 4);
+    }
+}
+
+// launch k of a solve (k = 0, 1, ... counted by the host)
 template <int D, typename T>
-__global__ void __launch_bounds__(kVT) cg_step(int64_t nn, T* x, T* r, T* z, T* p, T* s, const T* w,
-                                               const T* Minv, CgState* st, double* partial,
+__global__ void __launch_bounds__(kVT) cg_step(int64_t nn, long long k, T* x, T* r, T* z, T* p, T* s, const T* w,
+                                               const T* Minv, CgState* st, typename AccT<T>::type* partial,
                                                const double* tile_red, int n_tiles) {
-    if (st->done) return;  // uniform: only the last block of a kernel writes done
-    const double gamma = st->gamma, delta = tile_total<T>(tile_red, n_tiles);
-    const int k = st->k;
-    const double beta = k == 0 ? 0.0 : gamma / st->gamma_old;
-    const double pKp = k == 0 ? delta : delta - beta * gamma / st->alpha;
-    typename AccT<T>::type v[2] = {};
-    double tot[2];
-    if (!(pKp > 0.0)) {
-        // non-positive curvature: stop; at the first iteration take d = P r
-        if (k == 0)
-            for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT)
+    using A = typename AccT<T>::type;
+    if (st->done) return;  // a stop taken by an earlier launch (or by this one: same decision)
+    __shared__ A sh[kVT / 32 * 3];
+    __shared__ T sh_step[2];
+    __shared__ int sh_code;
+    const int nb = gridDim.x;
+    // thread 0's scalars of the previous launch, loaded before the sums
+    double rgamma_old = 0.0, pkp_old = 0.0, tol2 = 0.0;
+    long long cg_max = 0;
+    if (threadIdx.x == 0) {
+        rgamma_old = st->rgamma[(k + 1) & 1];
+        pkp_old = st->pkp[(k + 1) & 1];
+        tol2 = st->tol2;
+        cg_max = st->cg_max;
+    }
+    // this thread's first group of nodes, loaded before the sums so that the
+    // loads overlap them (groups of G nodes with 16-byte accesses)
+    constexpr int G = node_group(D, (int)sizeof(T)), E = G * D;
+    const int64_t ng = nn / G, gstride = (int64_t)gridDim.x * kVT;
+    int64_t gi = blockIdx.x * (int64_t)kVT + threadIdx.x;
+    T zv[E], pv[E], sv[E], wv[E], xv[E], rv[E];
+    if (gi < ng) {
+        const int64_t i0 = gi * E;
+        ld16(z + i0, zv);
+        ld16(p + i0, pv);
+        ld16(s + i0, sv);
+        ld16(w + i0, wv);
+        ld16(x + i0, xv);
+        ld16(r + i0, rv);
+    }
+    // r . r and r . z of the current residual (the previous kernel's block
+    // partials, slot k & 1) and z . K z (the HVP's tile partials); loads in
+    // batches of kB before the adds, so that they are in flight together
+    constexpr int kB = 8;
+    A acc[3] = {};
+    const A* pin = partial + (size_t)(k & 1) * kVecBlocks * 2;
+    for (int i = threadIdx.x; i < nb; i += kVT) {
+        acc_add(acc[0], ld_acc(pin + 2 * i));
+        acc_add(acc[1], ld_acc(pin + 2 * i + 1));
+    }
+    for (int t0 = threadIdx.x; t0 < n_tiles; t0 += kB * kVT) {
+        A q[kB];
 #pragma unroll
-                for (int c = 0; c < D; ++c) x[n * D + c] = z[n * D + c];
-        if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
-            st->k = k + 1;
-            st->done = 2;
+        for (int j = 0; j < kB; ++j) q[j] = t0 + j * kVT < n_tiles ? tile_partial<T>(tile_red, t0 + j * kVT) : A{};
+#pragma unroll
+        for (int j = 0; j < kB; ++j) acc_add(acc[2], q[j]);
+    }
+    block_sum<3>(acc, sh);
+    // the scalar recurrences run in thread 0 alone and reach the block as
+    // steps in the CG type.  With pkp = p^T K p and rgamma = 1 / gamma kept
+    // from the previous launch: beta = gamma rgamma_old, beta gamma /
+    // alpha_old = beta^2 pkp_old, so the only division on this path is
+    // alpha = gamma / p^T K p (in the CG type; FP64 issues slowly here).
+    double rr = 0.0, gamma = 0.0, pKp = 0.0;
+    if (threadIdx.x == 0) {
+        rr = widen(acc[0]);
+        gamma = widen(acc[1]);
+        const double delta = widen(acc[2]);
+        int code = 0;
+        double beta = 0.0;
+        T alpha = T(0);
+        if (rr <= tol2) {
+            code = 1;
+        } else if (k >= cg_max) {
+            code = 3;
+        } else {
+            beta = k == 0 ? 0.0 : gamma * rgamma_old;
+            pKp = k == 0 ? delta : delta - beta * beta * pkp_old;
+            if (pKp > 0.0)
+                alpha = (T)gamma / (T)pKp;
+            else
+                code = 2;  // non-positive curvature
+        }
+        sh_code = code;
+        sh_step[0] = alpha;
+        sh_step[1] = (T)beta;
+    }
+    __syncthreads();
+    const int code = sh_code;
+    if (code) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->rr = rr;
+            st->k = code == 2 ? (int)k + 1 : (int)k;  // HVPs spent (the curvature test used this one)
+            st->done = code;
         }
         return;
     }
-    const double alpha = gamma / pKp;
-    const T a = (T)alpha, bt = (T)beta;
-    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+    const T a = sh_step[0], bt = sh_step[1];
+    A v[2] = {};
+    while (gi < ng) {
+        const int64_t i0 = gi * E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            pv[e] = zv[e] + bt * pv[e];
+            sv[e] = wv[e] + bt * sv[e];
+            xv[e] += a * pv[e];
+            rv[e] -= a * sv[e];
+        }
+        st16(p + i0, pv);
+        st16(s + i0, sv);
+        st16(x + i0, xv);
+        st16(r + i0, rv);
+        T Mv[E * D];
+        ld16(Minv + gi * E * D, Mv);
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                T t = Mv[(q * D + i) * D] * rv[q * D];
+#pragma unroll
+                for (int j = 1; j < D; ++j) t += Mv[(q * D + i) * D + j] * rv[q * D + j];
+                zv[q * D + i] = t;
+            }
+        st16(z + i0, zv);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            acc_prod(v[0], rv[e], rv[e]);
+            acc_prod(v[1], rv[e], zv[e]);
+        }
+        gi += gstride;
+        if (gi < ng) {  // the next group
+            const int64_t i1 = gi * E;
+            ld16(z + i1, zv);
+            ld16(p + i1, pv);
+            ld16(s + i1, sv);
+            ld16(w + i1, wv);
+            ld16(x + i1, xv);
+            ld16(r + i1, rv);
+        }
+    }
+    for (int64_t n = ng * G + blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
         T rv[3] = {0, 0, 0}, zz[3];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -315,17 +494,14 @@ __global__ void __launch_bounds__(kVT) cg_step(int64_t nn, T* x, T* r, T* z, T* 
             acc_prod(v[1], rv[c], zz[c]);
         }
     }
-    if (grid_total<2>(v, tot, partial, &st->counter) && threadIdx.x == 0) {
-        const int k1 = k + 1;
-        st->k = k1;
-        st->rr = tot[0];
-        if (sqrt(tot[0]) <= st->tol) {
-            st->done = 1;
-        } else {
-            st->gamma_old = gamma;
-            st->gamma = tot[1];
-            st->alpha = alpha;
-            if (k1 >= st->cg_max) st->done = 3;
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        A* pout = partial + (size_t)((k + 1) & 1) * kVecBlocks * 2;
+        pout[2 * blockIdx.x] = v[0];
+        pout[2 * blockIdx.x + 1] = v[1];
+        if (blockIdx.x == 0) {  // read by launch k + 1
+            st->rgamma[k & 1] = 1.0 / gamma;
+            st->pkp[k & 1] = pKp;
         }
     }
 }
@@ -554,7 +730,8 @@ fem_status ensure_work(fem_mesh* m, int cg_dtype) {
         FEM_TRY(dalloc(w, &w->t, w->nd));
         FEM_TRY(dalloc(w, &w->du, w->nd));
         FEM_TRY(dalloc(w, &w->ut, w->nd));
-        FEM_TRY(dalloc(w, &w->partial, (size_t)kMaxRedBlocks * 2));
+        // dot_kernel: kMaxRedBlocks slots; PCG: 2 x kVecBlocks x 2 (8-byte) slots
+        FEM_TRY(dalloc(w, &w->partial, (size_t)std::max(kMaxRedBlocks, 2 * kVecBlocks) * 2));
         FEM_TRY(dalloc(w, &w->cg, 1));
         FEM_TRY(dalloc(w, &w->dot, 1));
         FEM_TRY(dalloc(w, &w->scal, 4));
@@ -758,17 +935,24 @@ private:
         return w_->h->bad ? 5 : 0;
     }
 
+    // grid of cg_init and cg_step (one group of node_group nodes per thread)
     template <int D, typename T>
-    fem_status launch_cg_iteration(const void* ucg) {
+    int cg_grid() const {
+        return grid_for(w_->nn / node_group(D, (int)sizeof(T)) + 1);
+    }
+
+    template <int D, typename T>
+    fem_status launch_cg_iteration(const void* ucg, long long k) {
         SolverWork* w = w_;
         const int pi = pi_;
+        using A = typename AccT<T>::type;
         // w = K z with z . K z (fused), then the update
         FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
                              st_, &w->cg->done, /*vkv_tiles=*/1));
-        cg_step<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
-                                                    (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
-                                                    (const T*)w->Minv[pi], w->cg, w->partial,
-                                                    femi::tile_partials(m_), m_->info.n_tiles);
+        cg_step<D, T><<<cg_grid<D, T>(), kVT, 0, st_>>>(w->nn, k, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
+                                                        (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
+                                                        (const T*)w->Minv[pi], w->cg, reinterpret_cast<A*>(w->partial),
+                                                        femi::tile_partials(m_), m_->info.n_tiles);
         CUDA_TRY(cudaGetLastError());
         return FEM_OK;
     }
@@ -780,19 +964,23 @@ private:
         SolverWork* w = w_;
         const int pi = pi_;
         SolverWork::Host* h = w->h;
-        h->cg.tol = tol;
+        h->cg.tol2 = tol * tol;
         h->cg.cg_max = cg_max_;
-        // only tol and cg_max are read before cg_init writes the rest
-        CUDA_TRY(cudaMemcpyAsync(&w->cg->tol, &h->cg.tol, sizeof(double), cudaMemcpyHostToDevice, st_));
+        // tol2 and cg_max are set per solve; cg_init resets done and k, and the
+        // rest is written by each launch before the next one reads it
+        CUDA_TRY(cudaMemcpyAsync(&w->cg->tol2, &h->cg.tol2, sizeof(double), cudaMemcpyHostToDevice, st_));
         CUDA_TRY(cudaMemcpyAsync(&w->cg->cg_max, &h->cg.cg_max, sizeof(long long), cudaMemcpyHostToDevice, st_));
-        cg_init<D, T><<<grid_nodes(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],
-                                                    (T*)w->z[pi], (T*)w->p[pi], (T*)w->s[pi], (const T*)w->Minv[pi],
-                                                    w->cg, w->partial);
+        using A = typename AccT<T>::type;
+        cg_init<D, T><<<cg_grid<D, T>(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],
+                                                        (T*)w->z[pi], (T*)w->p[pi], (T*)w->s[pi],
+                                                        (const T*)w->Minv[pi], w->cg, reinterpret_cast<A*>(w->partial));
         CUDA_TRY(cudaGetLastError());
         const int B = o_.cg_batch > 0 ? o_.cg_batch : 8;
+        // the stop is seen one launch after the update that reaches it: the
+        // launches run past cg_max so that the cap is always taken
         const int64_t max_batches = cg_max_ / B + 3;
         for (int64_t j = 0; j < max_batches; ++j) {
-            for (int i = 0; i < B; ++i) FEM_TRY((launch_cg_iteration<D, T>(ucg)));
+            for (int i = 0; i < B; ++i) FEM_TRY((launch_cg_iteration<D, T>(ucg, (long long)(j * B + i))));
             CUDA_TRY(cudaMemcpyAsync(&h->done[j & 1], &w->cg->done, sizeof(int), cudaMemcpyDeviceToHost, st_));
             CUDA_TRY(cudaEventRecord(w->ev[j & 1], st_));
             if (j >= 1) {
@@ -803,6 +991,8 @@ private:
         CUDA_TRY(cudaMemcpyAsync(&h->cg, w->cg, sizeof(CgState), cudaMemcpyDeviceToHost, st_));
         FEM_TRY(sync());
         if (!h->cg.done) return fail(FEM_ERR_CUDA, "PCG ended without a final state");
+        if (h->cg.done == 2 && h->cg.k == 1)  // curvature test failed at once: take d = M b
+            CUDA_TRY(cudaMemcpyAsync(w->x[pi], w->z[pi], (size_t)w->nd * sizeof(T), cudaMemcpyDeviceToDevice, st_));
         *iters = h->cg.k;
         return FEM_OK;
     }
