@@ -933,6 +933,9 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const int G = gridDim.x, cta = blockIdx.x;
     const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
     if (n_my == 0) return;
+    // under a programmatic dependent launch the CTAs start while the previous
+    // kernel drains; nothing it writes is touched before this point
+    grid_dependency_wait();
     if (p.skip != nullptr && *p.skip != 0) return;  // uniform: set by an earlier kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes);

@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(kVT) cg_step(int64_t nn, long long k, T* x, T*
                                                const T* Minv, CgState* st, typename AccT<T>::type* partial,
                                                const double* tile_red, int n_tiles) {
     using A = typename AccT<T>::type;
+    fem::grid_dependency_wait();  // launched as a programmatic dependent launch
     if (st->done) return;  // a stop taken by an earlier launch (or by this one: same decision)
     __shared__ A sh[kVT / 32 * 3];
     __shared__ T sh_step[2];
@@ -947,13 +948,23 @@ private:
         const int pi = pi_;
         using A = typename AccT<T>::type;
         // w = K z with z . K z (fused), then the update
+        // (both as programmatic dependent launches: each kernel's blocks are
+        // placed while the previous kernel drains)
         FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
-                             st_, &w->cg->done, /*vkv_tiles=*/1));
-        cg_step<D, T><<<cg_grid<D, T>(), kVT, 0, st_>>>(w->nn, k, (T*)w->x[pi], (T*)w->res[pi], (T*)w->z[pi],
-                                                        (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
-                                                        (const T*)w->Minv[pi], w->cg, reinterpret_cast<A*>(w->partial),
-                                                        femi::tile_partials(m_), m_->info.n_tiles);
-        CUDA_TRY(cudaGetLastError());
+                             st_, &w->cg->done, /*vkv_tiles=*/1, /*pdl=*/1));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cg_grid<D, T>());
+        cfg.blockDim = dim3(kVT);
+        cfg.stream = st_;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CUDA_TRY(cudaLaunchKernelEx(&cfg, cg_step<D, T>, (int64_t)w->nn, k, (T*)w->x[pi], (T*)w->res[pi],
+                                    (T*)w->z[pi], (T*)w->p[pi], (T*)w->s[pi], (const T*)w->q[pi],
+                                    (const T*)w->Minv[pi], w->cg, reinterpret_cast<A*>(w->partial),
+                                    femi::tile_partials(m_), m_->info.n_tiles));
         return FEM_OK;
     }
 
