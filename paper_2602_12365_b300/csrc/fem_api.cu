@@ -325,7 +325,7 @@ fem_status static_scratch(ReductionScratch* out) {
 fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
                   double* out_scalar, double* out_mu, double* out_lam, unsigned flags,
                   cudaStream_t st, const ReductionScratch* scratch = nullptr, const int* skip = nullptr,
-                  int vkv_tiles = 0, int pdl = 0) {
+                  int vkv_tiles = 0) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
     if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
@@ -399,9 +399,10 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         grid = std::min(p.n_tiles, ri->second);
         grid = std::max(grid, (p.n_tiles + fem::kMaxTilesPerCta - 1) / fem::kMaxTilesPerCta);
     }
-    if (pdl) {
+    {
         // programmatic dependent launch: the CTAs are placed as the previous
-        // kernel's blocks exit and wait on griddepcontrol.wait
+        // kernel's blocks exit and wait on griddepcontrol.wait before their
+        // first access to anything an earlier kernel writes
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3(fem::kThreads);
@@ -413,10 +414,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, p));
-    } else {
-        fn<<<grid, fem::kThreads, smem, st>>>(p);
     }
-    CUDA_TRY(cudaGetLastError());
     if (op == fem::OP_RESIDUAL || op == fem::OP_HVP || op == fem::OP_BLOCKDIAG) {
         // shared nodes: programmatic dependent launch, so the launch overlaps
         // the tile kernel's tail; the kernel waits on griddepcontrol.wait
@@ -480,8 +478,8 @@ namespace femi {
 fem_status set_error(fem_status s, const std::string& msg) { return fail(s, msg); }
 
 fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
-                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip, int vkv_tiles, int pdl) {
-    return launch(m, dtype, op, u, v, out, out_scalar, nullptr, nullptr, flags, st, nullptr, skip, vkv_tiles, pdl);
+                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip, int vkv_tiles) {
+    return launch(m, dtype, op, u, v, out, out_scalar, nullptr, nullptr, flags, st, nullptr, skip, vkv_tiles);
 }
 
 const double* tile_partials(const fem_mesh* m) { return m->tile_red; }

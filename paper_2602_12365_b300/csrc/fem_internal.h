@@ -64,12 +64,10 @@ fem_status set_error(fem_status s, const std::string& msg);
 // device pointer, the kernels return at once if *skip is non-zero
 // (vkv_tiles: for the HVP, leave the per-tile vKv partials in
 // tile_partials(m) -- FP32 (hi, lo) pairs for FP32 calls, doubles for FP64,
-// one per tile at a stride of 4 doubles -- for the caller to reduce;
-// pdl: launch the tile kernel as a programmatic dependent launch of the
-// previous kernel on `st`)
+// one per tile at a stride of 4 doubles -- for the caller to reduce).  The
+// tile kernel and its finalize kernel are programmatic dependent launches.
 fem_status run_op(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* out,
-                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip, int vkv_tiles = 0,
-                  int pdl = 0);
+                  double* out_scalar, unsigned flags, cudaStream_t st, const int* skip, int vkv_tiles = 0);
 const double* tile_partials(const fem_mesh* m);
 // frees the Newton-CG workspace of `m` (no-op without one)
 void solver_free(fem_mesh* m);
