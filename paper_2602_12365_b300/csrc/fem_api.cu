@@ -345,8 +345,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.stride = m->stride;
     p.has_mat = m->per_elem_mat ? 1 : 0;
     p.slot_owner = m->slot_owner;
-    p.shared_gid = m->shared_gid;
-    p.shared_slot_ptr = m->shared_slot_ptr;
+    p.shared_info = m->shared_info;
     p.n_shared = (int)m->plan.shared_gid.size();
     p.orphans = m->orphans;
     p.n_orphans = (int)m->plan.orphans.size();
@@ -605,8 +604,15 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
     UP(round_nvalid, P.round_nvalid);
     UP(round_elem, P.round_elem);
     UP(slot_owner, P.slot_owner);
-    UP(shared_gid, P.shared_gid);
-    UP(shared_slot_ptr, P.shared_slot_ptr);
+    {
+        // one 16-byte record per shared node, so that the finalize kernel
+        // issues its slot loads after a single load
+        std::vector<int4> info(P.shared_gid.size());
+        for (size_t j = 0; j < info.size(); ++j)
+            info[j] = make_int4((int)P.shared_slot_ptr[j], (int)P.shared_slot_ptr[j + 1], P.shared_gid[j],
+                                (int)mask[P.shared_gid[j]]);
+        UP(shared_info, info);
+    }
     UP(orphans, P.orphans);
     UP(node_mask, mask);
     {

@@ -30,8 +30,7 @@ struct fem_mesh {
     uint8_t* round_nvalid = nullptr;
     int32_t* round_elem = nullptr;
     int32_t* slot_owner = nullptr;
-    int32_t* shared_gid = nullptr;
-    int64_t* shared_slot_ptr = nullptr;
+    int4* shared_info = nullptr;  // per shared node: first slot, end slot, node, Dirichlet bits
     int32_t* orphans = nullptr;
     uint8_t* node_mask = nullptr;
     uint8_t* node_mask_local = nullptr;

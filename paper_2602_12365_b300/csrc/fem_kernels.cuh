@@ -154,8 +154,7 @@ struct KParams {
     int stride;
     int has_mat;
     const int32_t* slot_owner;
-    const int32_t* shared_gid;
-    const int64_t* shared_slot_ptr;
+    const int4* shared_info;  // [n_shared] first slot, end slot, node, Dirichlet bits
     int n_shared;
     const int32_t* orphans;
     int n_orphans;
@@ -1404,21 +1403,32 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) 
     const int total = p.n_shared + p.n_orphans;
     for (int j = blockIdx.x * kFinThreads + threadIdx.x; j < total; j += gridDim.x * kFinThreads) {
         if (j < p.n_shared) {
-            const int64_t s0 = p.shared_slot_ptr[j], s1 = p.shared_slot_ptr[j + 1];
+            const int4 inf = __ldg(p.shared_info + j);
+            const int s0 = inf.x, s1 = inf.y, g = inf.z;
+            const uint8_t m = (uint8_t)inf.w;
             T sum[6] = {0, 0, 0, 0, 0, 0};
-            for (int64_t q = s0; q < s1; ++q) {
-                if constexpr (OP == OP_BLOCKDIAG) {
+            // slots in batches of kFinBatch: the loads of a batch are issued
+            // together, then added in slot order
+            constexpr int kFinBatch = 4;
+            for (int q0 = s0; q0 < s1; q0 += kFinBatch) {
+                T t[kFinBatch][AW > 4 ? AW : 4];
 #pragma unroll
-                    for (int c = 0; c < AW; ++c) sum[c] += part[q * AW + c];
-                } else {
-                    T t[4];
-                    lds_vec<VW, T>(part, (int)q, t);
+                for (int b = 0; b < kFinBatch; ++b) {
+                    if (q0 + b >= s1) break;
+                    if constexpr (OP == OP_BLOCKDIAG) {
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) sum[c] += t[c];
+                        for (int c = 0; c < AW; ++c) t[b][c] = part[(int64_t)(q0 + b) * AW + c];
+                    } else {
+                        lds_vec<VW, T>(part, q0 + b, t[b]);
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < kFinBatch; ++b) {
+                    if (q0 + b >= s1) break;
+#pragma unroll
+                    for (int c = 0; c < AW; ++c) sum[c] += t[b][c];
                 }
             }
-            const int g = p.shared_gid[j];
-            const uint8_t m = p.node_mask[g];
             if constexpr (OP == OP_BLOCKDIAG)
                 fl |= write_block<D, T>(out, g, sum, m);
             else
