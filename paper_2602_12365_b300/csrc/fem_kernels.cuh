@@ -932,10 +932,6 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const int G = gridDim.x, cta = blockIdx.x;
     const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
     if (n_my == 0) return;
-    // under a programmatic dependent launch the CTAs start while the previous
-    // kernel drains; nothing it writes is touched before this point
-    grid_dependency_wait();
-    if (p.skip != nullptr && *p.skip != 0) return;  // uniform: set by an earlier kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes);
     const int AW = L.aw;
@@ -1041,10 +1037,15 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
         ++issued;
     };
 
-    // 1. start: metadata of the first two tiles, the ring, tile 0's gathers
+    // 1. start: metadata of the first two tiles, the ring, tile 0's gathers.
+    // Under a programmatic dependent launch the CTAs start while the previous
+    // kernel drains: up to here only mesh data (plan, metadata) is read, and
+    // nothing an earlier kernel writes is touched before the wait.
     Meta cur, nxt;
     load_meta(0, cur);
     if (n_my > 1) load_meta(1, nxt);
+    grid_dependency_wait();
+    if (p.skip != nullptr && *p.skip != 0) return;  // uniform: set by an earlier kernel
     if (lane == 0)
         for (int k = 0; k < kStages; ++k) issue_next();
     gather(0, cur);
@@ -1395,15 +1396,20 @@ template <int D, typename T, int OP>
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const KParams p) {
     constexpr int VW = D == 2 ? 2 : 4;
     constexpr int AW = (OP == OP_BLOCKDIAG) ? (D == 2 ? 4 : 6) : VW;
+    const int total = p.n_shared + p.n_orphans;
+    const int j0 = blockIdx.x * kFinThreads + threadIdx.x;
+    // the shared-node records are mesh data: the first one is loaded while
+    // the tile kernel drains
+    int4 inf = make_int4(0, 0, 0, 0);
+    if (j0 < p.n_shared) inf = __ldg(p.shared_info + j0);
     grid_dependency_wait();  // the tile kernel's writes are visible past this point
     if (p.skip != nullptr && *p.skip != 0) return;
     const T* part = static_cast<const T*>(p.partial);
     T* out = static_cast<T*>(p.out);
     int fl = 0;
-    const int total = p.n_shared + p.n_orphans;
-    for (int j = blockIdx.x * kFinThreads + threadIdx.x; j < total; j += gridDim.x * kFinThreads) {
+    for (int j = j0; j < total; j += gridDim.x * kFinThreads) {
         if (j < p.n_shared) {
-            const int4 inf = __ldg(p.shared_info + j);
+            if (j != j0) inf = __ldg(p.shared_info + j);
             const int s0 = inf.x, s1 = inf.y, g = inf.z;
             const uint8_t m = (uint8_t)inf.w;
             T sum[6] = {0, 0, 0, 0, 0, 0};

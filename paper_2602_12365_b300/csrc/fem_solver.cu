@@ -344,7 +344,13 @@ __global__ void __launch_bounds__(kVT) cg_step(int64_t nn, long long k, T* x, T*
                                                const T* Minv, CgState* st, typename AccT<T>::type* partial,
                                                const double* tile_red, int n_tiles) {
     using A = typename AccT<T>::type;
-    fem::grid_dependency_wait();  // launched as a programmatic dependent launch
+    // Launched as a programmatic dependent launch of the HVP's finalize
+    // kernel.  Its blocks start only once every finalize block has exited, and
+    // each of those first waited for the HVP's tile kernel, which itself
+    // waited for the previous update kernel (or cg_init) to complete.  So
+    // what that update kernel wrote (x, r, z, p, s, the block partials, the
+    // state) is visible from the start; w and the tile partials only after
+    // griddepcontrol.wait.
     if (st->done) return;  // a stop taken by an earlier launch (or by this one: same decision)
     __shared__ A sh[kVT / 32 * 3];
     __shared__ T sh_step[2];
@@ -370,10 +376,11 @@ __global__ void __launch_bounds__(kVT) cg_step(int64_t nn, long long k, T* x, T*
         ld16(z + i0, zv);
         ld16(p + i0, pv);
         ld16(s + i0, sv);
-        ld16(w + i0, wv);
         ld16(x + i0, xv);
         ld16(r + i0, rv);
     }
+    fem::grid_dependency_wait();
+    if (gi < ng) ld16(w + gi * E, wv);
     // r . r and r . z of the current residual (the previous kernel's block
     // partials, slot k & 1) and z . K z (the HVP's tile partials); loads in
     // batches of kB before the adds, so that they are in flight together
