@@ -75,6 +75,12 @@ def lib():
         L.ora_lp_blocks.restype = i32
         L.ora_lp_blocks.argtypes = [i64, P, P, P, P]
         L.ora_lp_blocks_backward.argtypes = [i64, P, P, P, P, P]
+        L.ora_dof_pattern.restype = i64
+        L.ora_dof_pattern.argtypes = [i64, i32, i64, i32, P, P, P, i64]
+        L.ora_distance2_colors.restype = i32
+        L.ora_distance2_colors.argtypes = [i64, P, P, P]
+        L.ora_sparse_values.restype = i32
+        L.ora_sparse_values.argtypes = mesh + [P, P, i32, i32, P, P, P, P]
         _lib = L
     return _lib
 
@@ -141,6 +147,19 @@ class OracleMesh:
         lib().ora_hvp(*self._args(), _p(u), _p(v), _p(self.mask), int(mask_in), int(mask_out),
                       _p(y), C.byref(st))
         return (y, st.value) if return_status else y
+
+    def sparse_K(self, u, mask_in=True, mask_out=True):
+        """(ptr, idx, vals): K(u) on the DOF pattern, column j = K e_j (slow:
+        one oracle HVP per DOF)."""
+        ptr, idx = dof_pattern(self.nn, self.dim, self.conn)
+        vals = np.zeros(idx.size)
+        st = C.c_int(0)
+        mk = self.mask if (mask_in or mask_out) else None
+        rc = lib().ora_sparse_values(*self._args(), _p(_f64(u)), _p(mk), int(mask_in), int(mask_out),
+                                     _p(ptr), _p(idx), _p(vals), C.byref(st))
+        if rc != 0:
+            raise RuntimeError("K e_j has entries outside the pattern")
+        return ptr, idx, vals
 
     def block_diag(self, u):
         u = _f64(u).reshape(-1)
@@ -273,3 +292,29 @@ def lp_blocks_backward(D, mask, o, gM):
     go = np.zeros((D.shape[0], 6))
     lib().ora_lp_blocks_backward(D.shape[0], _p(D), None if mk is None else _p(mk), _p(o), _p(gM), _p(go))
     return go
+
+
+# ----------------------------------------------------------------------------
+# sparse K by colouring (Sec. 2.2, Algorithm 2; App. A, B)
+# ----------------------------------------------------------------------------
+def dof_pattern(n_nodes, dim, conn):
+    """CSR (ptr, idx) of the DOF pattern of K: entry (i, j) when the nodes of
+    DOFs i and j share an element."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    ne, n_en = conn.shape
+    ptr = np.zeros(n_nodes * dim + 1, np.int64)
+    m = lib().ora_dof_pattern(n_nodes, dim, ne, n_en, _p(conn), _p(ptr), None, 0)
+    idx = np.zeros(max(m, 1), np.int32)
+    lib().ora_dof_pattern(n_nodes, dim, ne, n_en, _p(conn), _p(ptr), _p(idx), m)
+    return ptr, idx[:m]
+
+
+def distance2_colors(ptr, idx):
+    """Greedy distance-2 column colouring in ascending column order:
+    (colors [n], n_colors)."""
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = ptr.size - 1
+    col = np.zeros(max(n, 1), np.int32)
+    nc = lib().ora_distance2_colors(n, _p(ptr), _p(idx), _p(col))
+    return col[:n], int(nc)

@@ -956,3 +956,122 @@ void ora_lp_blocks_backward(int64_t nn, const double* D, const uint8_t* mask, co
         g[5] = W[8] * sig5;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Sparse K by colouring (Sec. 2.2, Algorithm 2; App. A and B).
+ * ------------------------------------------------------------------------ */
+
+/* The DOF pattern of App. B: K_ij, i = n d + a, j = m d + b, can be
+ * non-zero only when nodes n and m lie in one element (n = m included). */
+int64_t ora_dof_pattern(int64_t nn, int d, int64_t ne, int n_en, const int32_t* conn,
+                        int64_t* ptr, int32_t* idx, int64_t cap) {
+    /* the node graph (other nodes of the node's elements), plus the node */
+    int64_t* gp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nn + 1));
+    int64_t m = ora_node_graph(nn, ne, n_en, conn, gp, NULL, 0);
+    int32_t* gi = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    ora_node_graph(nn, ne, n_en, conn, gp, gi, m);
+    int32_t* row = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    int64_t k = 0;
+    ptr[0] = 0;
+    for (int64_t n = 0; n < nn; ++n) {
+        /* nodes of row n in ascending order: the neighbours and n itself */
+        int64_t len = 0;
+        int used_self = 0;
+        for (int64_t q = gp[n]; q < gp[n + 1]; ++q) {
+            if (!used_self && gi[q] > n) {
+                row[len++] = (int32_t)n;
+                used_self = 1;
+            }
+            row[len++] = gi[q];
+        }
+        if (!used_self) row[len++] = (int32_t)n;
+        for (int a = 0; a < d; ++a) {
+            for (int64_t q = 0; q < len; ++q)
+                for (int b = 0; b < d; ++b) {
+                    if (idx && k < cap) idx[k] = row[q] * d + b;
+                    ++k;
+                }
+            ptr[n * d + a + 1] = k;
+        }
+    }
+    free(row);
+    free(gi);
+    free(gp);
+    return k;
+}
+
+/* Greedy distance-2 colouring of the columns (App. A): columns in ascending
+ * order; column j takes the smallest colour that no earlier column sharing a
+ * row with it holds.  The pattern is symmetric, so the rows of column j are
+ * the entries of row j. */
+int ora_distance2_colors(int64_t n, const int64_t* ptr, const int32_t* idx, int32_t* colors) {
+    int ncol = 0;
+    int cap = 64;
+    int64_t* seen = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    for (int c = 0; c < cap; ++c) seen[c] = -1;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) {
+            int64_t i = idx[q];
+            for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+                int64_t k = idx[t];
+                if (k < j) seen[colors[k]] = j; /* colour taken in j's rows */
+            }
+        }
+        int c = 0;
+        while (c < cap && seen[c] == j) ++c;
+        if (c == cap) {
+            seen = (int64_t*)realloc(seen, sizeof(int64_t) * (size_t)(2 * cap));
+            for (int t = cap; t < 2 * cap; ++t) seen[t] = -1;
+            cap *= 2;
+        }
+        colors[j] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(seen);
+    return ncol;
+}
+
+/* K (masked as in ora_hvp) on the pattern, column by column from its
+ * definition: column j is K e_j (ora_hvp with v = e_j).  Slow: n_dofs HVPs.
+ * Returns 0, or 5 when some K e_j is non-zero outside the pattern. */
+int ora_sparse_values(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                      const int32_t* conn, const double* mu, const double* lam,
+                      const double* u, const uint8_t* mask, int mask_in, int mask_out,
+                      const int64_t* ptr, const int32_t* idx, double* vals, int* status) {
+    int d = ora_dim(etype);
+    int64_t nd = n_nodes * d;
+    double* e = (double*)calloc((size_t)nd, sizeof(double));
+    double* y = (double*)malloc(sizeof(double) * (size_t)nd);
+    uint8_t* in_row = (uint8_t*)calloc((size_t)nd, 1);
+    int rc = 0, st = 0;
+    for (int64_t j = 0; j < nd; ++j) {
+        e[j] = 1.0;
+        int sj = 0;
+        ora_hvp(etype, n_nodes, n_el, X, conn, mu, lam, u, e, mask, mask_in, mask_out, y, &sj);
+        if (sj) st = sj;
+        e[j] = 0.0;
+        /* rows of column j = entries of row j (symmetric pattern) */
+        for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) in_row[idx[q]] = 1;
+        for (int64_t i = 0; i < nd; ++i)
+            if (!in_row[i] && y[i] != 0.0) rc = 5;
+        for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) in_row[idx[q]] = 0;
+        /* K_ij sits in row i at column j */
+        for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) {
+            int64_t i = idx[q];
+            int64_t lo = ptr[i], hi = ptr[i + 1];
+            while (lo < hi) { /* column j in row i */
+                int64_t mid = (lo + hi) / 2;
+                if (idx[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            vals[lo] = y[i];
+        }
+    }
+    free(in_row);
+    free(y);
+    free(e);
+    if (status) *status = st;
+    return rc;
+}

@@ -140,6 +140,22 @@ int ora_lp_blocks(int64_t nn, const double* D, const uint8_t* mask, const double
 void ora_lp_blocks_backward(int64_t nn, const double* D, const uint8_t* mask, const double* o,
                             const double* gM, double* go);
 
+/* Sparse K by colouring (Sec. 2.2, Algorithm 2; App. A, B).
+ * DOF pattern (App. B): CSR over DOFs (dof = node*dim + component), entry
+ * (i, j) when the nodes of i and j share an element (the node itself
+ * included), ascending columns; idx may be NULL to count.  Returns nnz. */
+int64_t ora_dof_pattern(int64_t nn, int d, int64_t ne, int n_en, const int32_t* conn,
+                        int64_t* ptr, int32_t* idx, int64_t cap);
+/* Greedy distance-2 colouring of the columns in ascending order (App. A);
+ * returns the number of colours. */
+int ora_distance2_colors(int64_t n, const int64_t* ptr, const int32_t* idx, int32_t* colors);
+/* K values on the pattern from K e_j = ora_hvp(e_j) for every column j
+ * (masking as ora_hvp); returns 5 if some K e_j leaves the pattern. */
+int ora_sparse_values(int etype, int64_t n_nodes, int64_t n_el, const double* X,
+                      const int32_t* conn, const double* mu, const double* lam,
+                      const double* u, const uint8_t* mask, int mask_in, int mask_out,
+                      const int64_t* ptr, const int32_t* idx, double* vals, int* status);
+
 #ifdef __cplusplus
 }
 #endif
