@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cells", dest="n", type=int, default=64, help="cells per side of the tet workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-K (Algorithm 2) measurement")
     ap.add_argument("--newton-steps", type=int, default=2,
                     help="load steps of the Newton-CG measurement per arm (0 = skip)")
     return ap.parse_args()
@@ -297,6 +298,47 @@ def newton_arms(n, n_steps, dev):
     return res
 
 
+def sparse_arm(gm, ut, vt, t_hvp_us, flush_l2, peak):
+    """Sparse K by colouring (Algorithm 2) on the benchmark mesh: host
+    pattern and colouring, the n_colors seeded HVPs plus decompression, and
+    the CSR product K v against the HVP (same FP32 u, v; L2 flushed before
+    each timed call)."""
+    import torch
+    t0 = time.perf_counter()
+    nnz, nc = gm.sparse_info()
+    t_host = time.perf_counter() - t0
+    vals = gm.sparse_assemble(ut)
+    y = gm.sparse_spmv(vals, vt)
+    h = gm.hvp(ut, vt)
+    rel = float(torch.linalg.norm(y - h) / torch.linalg.norm(h))
+
+    def timed(fn, reps):
+        ts = []
+        for k in range(reps):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(ts)
+
+    t_asm = timed(lambda: gm.sparse_assemble(ut, out=vals), 5)
+    t_spmv = timed(lambda: gm.sparse_spmv(vals, vt, out=y), 20)
+    nn = gm.n_nodes
+    n_blocks = nnz // 9  # node pairs: one node id each
+    spmv_bytes = nnz * 4 + n_blocks * 4 + (nn + 1) * 8 + nn * 8 + 2 * gm.n_dofs * 4
+    return {"what": "Algorithm 2: greedy distance-2 column colouring, one seeded HVP per colour, "
+                    "decompression into CSR; then y = K v (CSR, FP32)",
+            "nnz": nnz, "n_colors": nc, "host_pattern_and_colouring_s": t_host,
+            "assemble_ms": t_asm / 1e3, "assemble_in_hvps": t_asm / t_hvp_us,
+            "spmv_us": t_spmv, "hvp_us": t_hvp_us, "spmv_vs_hvp_rel_err": rel,
+            "spmv_roofline": {"bound": "hbm", "bytes": spmv_bytes, "achieved": spmv_bytes / (t_spmv * 1e-6) / 1e9,
+                              "peak": peak, "unit": "GB/s",
+                              "frac": spmv_bytes / (t_spmv * 1e-6) / 1e9 / peak}}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_init(args)
@@ -432,6 +474,8 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
+    if not args.no_sparse and rank == 0:  # a per-GPU measurement, reported by rank 0
+        line["sparse"] = sparse_arm(gm, ut, vt, t_hvp * 1e3, flush_l2, peak)
     if args.newton_steps > 0 and rank == 0:  # a per-GPU measurement, reported by rank 0
         line["newton"] = newton_arms(args.n, args.newton_steps, dev)
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -389,6 +389,47 @@ fem_status fem_lp_gradient(fem_lp* lp, fem_mesh* mesh, const float* u, const flo
 fem_status fem_lp_train_step(fem_lp* lp, fem_mesh* mesh, const float* u, const float* r, float lr,
                              double* loss, void* stream);
 
+/*
+ * Sparse K by colouring -- the paper's second route to the tangent (Sec. 2.2,
+ * Algorithm 2; App. A for the colouring, App. B for the pattern).
+ *
+ * Pattern: CSR over DOFs (dof = node * dim + component).  Entry (i, j) is
+ * present when the nodes of DOFs i and j lie in a common element (a node with
+ * itself included); the columns of every row ascend.  Colours: the greedy
+ * distance-2 colouring of the columns -- columns in ascending order, each
+ * takes the smallest colour not held by an earlier column that shares a row
+ * with it -- so no two columns of one colour share a row.  Both are built on
+ * the host by the first fem_sparse_* call on a mesh (time and host memory
+ * O(nnz)) and kept, with device copies, until fem_mesh_destroy.
+ *
+ * fem_sparse_info: *nnz (entries) and *n_colors; either may be NULL.
+ * fem_sparse_pattern: HOST copies; row_ptr int64 [n_dofs + 1], col_idx int32
+ *   [nnz], colors int32 [n_dofs]; each may be NULL.
+ * fem_sparse_assemble: Algorithm 2 on the device at the state u (DEVICE,
+ *   dtype): for each colour c, the seed e_c (1 on the DOFs of colour c) and
+ *   one HVP  Mo K(u) Mi e_c  (flags as fem_hvp), kept as column c of the
+ *   compressed Jacobian [n_colors][n_dofs] (mesh workspace, allocated on first
+ *   use per dtype); then values[k] = Jcomp[colour(col_idx[k])][row(k)].
+ *   values: DEVICE [nnz] of dtype, in the pattern's order.  Status bits of
+ *   the HVPs accumulate as for fem_hvp.
+ * fem_sparse_spmv: y = K x with the mesh's pattern and `values`; x, y DEVICE
+ *   [n_dofs] of dtype, not aliased.  Per row a fixed summation order.
+ * Errors: FEM_ERR_ARG (null or bad arguments; FEM_F32 on an FP64 mesh),
+ * FEM_ERR_BADMESH (more than 2^31 - 1 DOFs), FEM_ERR_CUDA.
+ */
+fem_status fem_sparse_info(fem_mesh* mesh, int64_t* nnz, int32_t* n_colors);
+/* The same pattern and colouring from a mesh description alone, on the host
+ * (no device, no handle): sizes in *nnz and *n_colors, arrays as for
+ * fem_sparse_pattern; every output may be NULL (call once with NULL arrays
+ * to size them). */
+fem_status fem_sparse_pattern_desc(const fem_mesh_desc* desc, int64_t* nnz, int32_t* n_colors,
+                                   int64_t* row_ptr, int32_t* col_idx, int32_t* colors);
+fem_status fem_sparse_pattern(fem_mesh* mesh, int64_t* row_ptr, int32_t* col_idx, int32_t* colors);
+fem_status fem_sparse_assemble(fem_mesh* mesh, int dtype, const void* u, unsigned flags, void* values,
+                               void* stream);
+fem_status fem_sparse_spmv(fem_mesh* mesh, int dtype, const void* values, const void* x, void* y,
+                           void* stream);
+
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */
 fem_status fem_sync_status(fem_mesh* mesh, void* stream, int32_t* flags);

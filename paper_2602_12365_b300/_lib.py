@@ -109,6 +109,11 @@ def lib():
             "fem_lp_gradient": [P, P, P, P, P, C.POINTER(C.c_double), P],
             "fem_newton_step": [P, P, P, C.c_double, C.c_double, C.POINTER(NewtonOpts),
                                 C.POINTER(NewtonStats), P],
+            "fem_sparse_info": [P, C.POINTER(C.c_int64), C.POINTER(i32)],
+            "fem_sparse_pattern": [P, P, P, P],
+            "fem_sparse_pattern_desc": [C.POINTER(MeshDesc), C.POINTER(C.c_int64), C.POINTER(i32), P, P, P],
+            "fem_sparse_assemble": [P, i32, P, u32, P, P],
+            "fem_sparse_spmv": [P, i32, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -130,4 +135,6 @@ EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_pla
             "fem_lp_create", "fem_lp_destroy", "fem_lp_set_loss", "fem_lp_set_clip",
             "fem_lp_get_params", "fem_lp_set_params",
             "fem_lp_features", "fem_lp_blocks", "fem_lp_gradient", "fem_lp_train_step",
+            "fem_sparse_info", "fem_sparse_pattern", "fem_sparse_pattern_desc", "fem_sparse_assemble",
+            "fem_sparse_spmv",
             "fem_last_error"]

@@ -683,6 +683,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     femi::solver_free(m);
     femi::lp_mesh_free(m);
+    femi::sparse_free(m);
     free_all(m);
     delete m;
     return FEM_OK;

@@ -12,6 +12,7 @@
 namespace femi {
 struct SolverWork;  // Newton-CG workspace, created on first use (fem_solver.cu)
 struct LpMeshData;  // learned-preconditioner graph on the device (fem_learned.cu)
+struct SparseData;  // sparse-K pattern, colouring and workspace (fem_sparse.cu)
 }
 
 struct fem_mesh {
@@ -54,6 +55,8 @@ struct fem_mesh {
     std::vector<int32_t> conn_host;
     std::vector<float> node_stats;
     femi::LpMeshData* lp = nullptr;
+    // sparse K by colouring (built by the first fem_sparse_* call)
+    femi::SparseData* sparse = nullptr;
 };
 
 namespace femi {
@@ -72,6 +75,8 @@ const double* tile_partials(const fem_mesh* m);
 void solver_free(fem_mesh* m);
 // frees the learned-preconditioner data of `m` (no-op without it)
 void lp_mesh_free(fem_mesh* m);
+// frees the sparse-K data of `m` (no-op without it)
+void sparse_free(fem_mesh* m);
 // fills the CG preconditioner blocks Minv [n_nodes * 9] (FP32) from the
 // learned network `lp` at the FP32 state u: block diagonal, features,
 // network, SPD map (fem_learned.cu)

@@ -79,6 +79,21 @@ def plan_partition(elem_type, coords, conn, tile_elems=0):
     return tile, rnd, lane, nodes, info.as_dict()
 
 
+def sparse_pattern_host(elem_type, coords, conn):
+    """Host-only DOF pattern of K and its greedy distance-2 column colouring
+    (no GPU): (row_ptr int64, col_idx int32, colors int32, n_colors)."""
+    d, keep = make_desc(elem_type, coords, conn)
+    nnz, nc = C.c_int64(0), C.c_int32(0)
+    L.check(L.lib().fem_sparse_pattern_desc(C.byref(d), C.byref(nnz), C.byref(nc), None, None, None))
+    n_dofs = d.n_nodes * (2 if int(elem_type) == 0 else 3)
+    rp = np.zeros(n_dofs + 1, np.int64)
+    ci = np.zeros(max(nnz.value, 1), np.int32)
+    co = np.zeros(n_dofs, np.int32)
+    L.check(L.lib().fem_sparse_pattern_desc(C.byref(d), None, None, rp.ctypes.data_as(C.c_void_p),
+                                            ci.ctypes.data_as(C.c_void_p), co.ctypes.data_as(C.c_void_p)))
+    return rp, ci[:nnz.value], co, nc.value
+
+
 class Mesh:
     """A mesh uploaded to the GPU (owns the C handle)."""
 
@@ -173,6 +188,45 @@ class Mesh:
         out = out if out is not None else torch.empty(self.n_nodes * self.dim * self.dim,
                                                       dtype=u.dtype, device=u.device)
         L.check(L.lib().fem_block_diag(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
+    # --- sparse K by colouring (Algorithm 2) ----------------------------------
+    def sparse_info(self):
+        """(nnz, n_colors) of K's DOF pattern and its distance-2 colouring
+        (built on the host by the first call)."""
+        nnz, nc = C.c_int64(0), C.c_int32(0)
+        L.check(L.lib().fem_sparse_info(self._h, C.byref(nnz), C.byref(nc)))
+        return nnz.value, nc.value
+
+    def sparse_pattern(self):
+        """Host numpy (row_ptr int64, col_idx int32, colors int32)."""
+        nnz, _ = self.sparse_info()
+        rp = np.zeros(self.n_dofs + 1, np.int64)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        co = np.zeros(self.n_dofs, np.int32)
+        L.check(L.lib().fem_sparse_pattern(self._h, rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                                           co.ctypes.data_as(C.c_void_p)))
+        return rp, ci[:nnz], co
+
+    def sparse_assemble(self, u, mask_in=True, mask_out=True, out=None, stream=None):
+        """CSR values of Mo K(u) Mi on the pattern (device, u's dtype): one
+        HVP per colour, then the decompression of Algorithm 2."""
+        self._check_vec(u)
+        nnz, _ = self.sparse_info()
+        out = out if out is not None else torch.empty(nnz, dtype=u.dtype, device=u.device)
+        if not (out.is_cuda and out.is_contiguous() and out.numel() == nnz and out.dtype == u.dtype):
+            raise ValueError("out must be a contiguous CUDA tensor of nnz entries in u's dtype")
+        flags = (L.FEM_MASK_IN if mask_in else 0) | (L.FEM_MASK_OUT if mask_out else 0)
+        L.check(L.lib().fem_sparse_assemble(self._h, _dtype_code(u), _ptr(u), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def sparse_spmv(self, values, x, out=None, stream=None):
+        """y = K x with the pattern and `values` (device, x's dtype)."""
+        self._check_vec(x)
+        if values.dtype != x.dtype or not (values.is_cuda and values.is_contiguous()):
+            raise TypeError("values must be a contiguous CUDA tensor of x's dtype")
+        out = out if out is not None else torch.empty_like(x)
+        L.check(L.lib().fem_sparse_spmv(self._h, _dtype_code(x), _ptr(values), _ptr(x), _ptr(out), _stream(stream)))
         return out
 
     def param_vjp(self, u, a, stream=None):

@@ -1,0 +1,117 @@
+"""Sparse K by colouring on the GPU (Algorithm 2) against the oracle.
+
+Bars: FP64 values within 1e-12 of the oracle's K (relative, in the
+Frobenius norm over the pattern; the values come from FP64 HVPs, so they
+differ from the oracle's only by summation order); FP32 values within 1e-5
+(FP32 element kernels).  The CSR product K v is checked against the GPU HVP
+in the same precision (the HVP itself is pinned to the oracle elsewhere), at
+small sizes and on the 64^3 benchmark mesh (K v = HVP(v) holds at any size).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_12365_b300 import meshgen as mg
+from paper_2602_12365_b300._lib import FemError
+from paper_2602_12365_b300.fem import Mesh, sparse_pattern_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(m, seed=1):
+    u = mg.smooth_state(m, 0.5, amp=0.05).ravel()
+    return u + 0.002 * np.random.default_rng(seed).standard_normal(u.size)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = [("tri", 4, {}), ("tet", 3, {"seed": 2, "random_moduli": 2}), ("hex", 2, {"seed": 1})]
+
+
+@pytest.mark.parametrize("kind,n,kw", CASES)
+@pytest.mark.parametrize("masked", [False, True])
+def test_assemble_fp64_matches_oracle(kind, n, kw, masked):
+    m = {"tri": mg.workload_tri, "tet": mg.workload_tet, "hex": mg.workload_hex}[kind](n, **kw)
+    gm = Mesh.from_fixture(m, precision="fp64")
+    u = _state(m)
+    vals = gm.sparse_assemble(torch.as_tensor(u, device="cuda"), mask_in=masked, mask_out=masked)
+    om = oracle.OracleMesh.from_mesh(m)
+    ptr, idx, ref = om.sparse_K(u, mask_in=masked, mask_out=masked)
+    rp, ci, co = gm.sparse_pattern()
+    assert np.array_equal(rp, ptr) and np.array_equal(ci, idx)
+    assert _rel(vals.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("kind,n,kw", CASES)
+def test_assemble_fp32_matches_oracle(kind, n, kw):
+    m = {"tri": mg.workload_tri, "tet": mg.workload_tet, "hex": mg.workload_hex}[kind](n, **kw)
+    gm = Mesh.from_fixture(m, precision="mixed")
+    u32 = torch.as_tensor(_state(m), dtype=torch.float32, device="cuda")
+    vals = gm.sparse_assemble(u32)
+    om = oracle.OracleMesh.from_mesh(m)
+    _, _, ref = om.sparse_K(u32.double().cpu().numpy())
+    assert _rel(vals.double().cpu().numpy(), ref) <= 1e-5
+
+
+def test_handle_pattern_equals_host_pattern():
+    m = mg.workload_tet(6, seed=4)
+    gm = Mesh.from_fixture(m)
+    rp, ci, co = gm.sparse_pattern()
+    rp2, ci2, co2, nc2 = sparse_pattern_host(m.elem_type, m.coords, m.conn)
+    nnz, nc = gm.sparse_info()
+    assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2) and np.array_equal(co, co2)
+    assert nnz == ci.size and nc == nc2 == co.max() + 1
+
+
+@pytest.mark.parametrize("precision,dt,tol", [("fp64", torch.float64, 1e-12), ("mixed", torch.float32, 1e-5)])
+def test_spmv_equals_hvp(precision, dt, tol):
+    m = mg.workload_tet(5, seed=3, random_moduli=3)
+    gm = Mesh.from_fixture(m, precision=precision)
+    u = torch.as_tensor(_state(m), dtype=dt, device="cuda")
+    vals = gm.sparse_assemble(u)
+    for s in range(3):
+        v = torch.as_tensor(np.random.default_rng(s).standard_normal(m.n_nodes * 3), dtype=dt, device="cuda")
+        y = gm.sparse_spmv(vals, v)
+        h = gm.hvp(u, v)
+        assert (torch.linalg.norm(y - h) / torch.linalg.norm(h)).item() <= tol
+
+
+def test_benchmark_mesh_properties():
+    """The 64^3 tet mesh (C2): 80-90 colours (App. A), K v = HVP(v) in FP32,
+    and K symmetric on sampled entries."""
+    m = mg.workload_tet(64)
+    gm = Mesh.from_fixture(m)
+    nnz, nc = gm.sparse_info()
+    n = 64
+    E = 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3
+    assert nnz == 9 * ((n + 1) ** 3 + 2 * E) and 80 <= nc <= 90
+    u = torch.as_tensor(mg.smooth_state(m, 0.5).ravel(), dtype=torch.float32, device="cuda")
+    vals = gm.sparse_assemble(u)
+    v = torch.as_tensor(mg.random_direction(m, 1).ravel(), dtype=torch.float32, device="cuda")
+    y, h = gm.sparse_spmv(vals, v), gm.hvp(u, v)
+    assert (torch.linalg.norm(y - h) / torch.linalg.norm(h)).item() <= 1e-5
+    rp, ci, _ = gm.sparse_pattern()
+    K = vals.cpu().numpy()
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, m.n_nodes * 3, 2000)
+    scale = np.abs(K).max()
+    for i in rows:
+        for k in range(rp[i], rp[i + 1], 7):
+            j = ci[k]
+            kj = rp[j] + np.searchsorted(ci[rp[j]:rp[j + 1]], i)
+            assert abs(K[k] - K[kj]) <= 1e-5 * scale
+
+
+def test_arguments_are_checked():
+    m = mg.workload_tet(2)
+    gm = Mesh.from_fixture(m)
+    u = torch.zeros(m.n_nodes * 3, dtype=torch.float32, device="cuda")
+    vals = gm.sparse_assemble(u)
+    with pytest.raises(FemError):
+        gm.sparse_spmv(vals, u, out=u)  # x and y alias
+    g64 = Mesh.from_fixture(m, precision="fp64")
+    with pytest.raises(FemError):
+        g64.sparse_assemble(u)  # FP32 on an FP64 mesh
