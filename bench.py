@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--cells", dest="n", type=int, default=64, help="cells per side of the tet workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-K (Algorithm 2) measurement")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the sparse-K (Algorithm 2) and atomic-scatter ablation measurements")
     ap.add_argument("--newton-steps", type=int, default=2,
                     help="load steps of the Newton-CG measurement per arm (0 = skip)")
     return ap.parse_args()
@@ -339,6 +340,37 @@ def sparse_arm(gm, ut, vt, t_hvp_us, flush_l2, peak):
                               "frac": spmv_bytes / (t_spmv * 1e-6) / 1e9 / peak}}
 
 
+def atomic_arm(gm, ut, vt, t_res_us, t_hvp_us, flush_l2):
+    """The scatter-add ablation: residual and HVP with one thread per element
+    and float atomics (fem_*_atomic) against the tiled, coloured calls timed
+    above (same inputs, L2 flushed before each timed call), and the entries
+    that change between two atomic runs."""
+    import torch
+    r = gm.residual_atomic(ut)
+    y = gm.hvp_atomic(ut, vt)
+
+    def timed(fn, reps=20):
+        ts = []
+        for k in range(reps):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(ts)
+
+    t_r = timed(lambda: gm.residual_atomic(ut, out=r))
+    t_h = timed(lambda: gm.hvp_atomic(ut, vt, out=y))
+    y2 = gm.hvp_atomic(ut, vt)
+    return {"what": "one thread per element in mesh order, nodal forces added with float atomicAdd "
+                    "(same constitutive code); the tiled kernels add in a fixed order",
+            "residual_us": t_r, "hvp_us": t_h, "tiled_residual_us": t_res_us, "tiled_hvp_us": t_hvp_us,
+            "slowdown_residual": t_r / t_res_us, "slowdown_hvp": t_h / t_hvp_us,
+            "hvp_entries_differing_between_two_runs": int((y2 != y).sum()), "n_dofs": gm.n_dofs}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_init(args)
@@ -474,7 +506,8 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
-    if not args.no_sparse and rank == 0:  # a per-GPU measurement, reported by rank 0
+    if not args.no_sparse and rank == 0:  # per-GPU measurements, reported by rank 0
+        line["atomic_ablation"] = atomic_arm(gm, ut, vt, t_res * 1e3, t_hvp * 1e3, flush_l2)
         line["sparse"] = sparse_arm(gm, ut, vt, t_hvp * 1e3, flush_l2, peak)
     if args.newton_steps > 0 and rank == 0:  # a per-GPU measurement, reported by rank 0
         line["newton"] = newton_arms(args.n, args.newton_steps, dev)

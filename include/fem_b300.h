@@ -430,6 +430,23 @@ fem_status fem_sparse_assemble(fem_mesh* mesh, int dtype, const void* u, unsigne
 fem_status fem_sparse_spmv(fem_mesh* mesh, int dtype, const void* values, const void* x, void* y,
                            void* stream);
 
+/*
+ * Ablation, not on the method's path: fem_residual / fem_hvp computed the
+ * traditional way of Sec. 5's comparison with scatter-add assembly -- one
+ * thread per element in mesh order, the element's nodal forces added into the
+ * output with floating-point atomicAdd (the output is zeroed first on
+ * `stream`).  Same constitutive code, arguments, flags and status bits as
+ * fem_residual / fem_hvp; P1 elements only (FEM_ERR_ARG for hexahedra).
+ * Results agree with the tiled kernels to rounding, but the order of the
+ * atomic additions, and so the last bits, can change from run to run.  The
+ * first call per precision builds per-element arrays in mesh order on the
+ * host (connectivity, grad N, w det J, moduli) and keeps them on the device.
+ */
+fem_status fem_residual_atomic(fem_mesh* mesh, int dtype, const void* u, void* r, unsigned flags,
+                               void* stream);
+fem_status fem_hvp_atomic(fem_mesh* mesh, int dtype, const void* u, const void* v, void* y, unsigned flags,
+                          void* stream);
+
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */
 fem_status fem_sync_status(fem_mesh* mesh, void* stream, int32_t* flags);

@@ -133,7 +133,9 @@ int elem_stride(int etype, bool mat) {
 // P1 gradients and weight for the vertex order the kernel uses (any
 // permutation of the element's vertices): grad N_a from the rows of J^-1,
 // w det J from |det J| (an odd permutation flips the sign of det J).
-void p1_record_geometry(int D, const double* Xe, double* out /* (NEN-1)*D + 1 */) {
+}  // namespace
+
+void femi::p1_geometry(int D, const double* Xe, double* out /* (NEN-1)*D + 1 */) {
     double g[4][3], wdJ;
     double J[3][3] = {{0}};
     for (int i = 0; i < D; ++i)
@@ -174,6 +176,8 @@ void p1_record_geometry(int D, const double* Xe, double* out /* (NEN-1)*D + 1 */
     out[D * D] = wdJ;
 }
 
+namespace {
+
 template <typename T>
 void pack_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out, int pi) {
     const fem::Plan& P = m->plan;
@@ -202,7 +206,7 @@ void pack_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out
                     const uint16_t* c = P.round_conn.data() + (r * 32 + l) * P.n_en_pad;
                     for (int a = 0; a <= D; ++a)
                         for (int k = 0; k < D; ++k) Xe[a * D + k] = d->coords[(size_t)gid[c[a]] * D + k];
-                    p1_record_geometry(D, Xe, geo);
+                    femi::p1_geometry(D, Xe, geo);
                     for (int k = 0; k * CW < NG; ++k) {
                         const int w = std::min(CW, NG - k * CW);
                         for (int j = 0; j < w; ++j) el0[32 * k * CW + l * w + j] = (T)geo[k * CW + j];
@@ -529,6 +533,11 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
         // host data of the learned preconditioner (one pass over the elements)
         const int ne_n = nen_of(d->elem_type);
         m->conn_host.assign(d->conn, d->conn + d->n_elems * ne_n);
+        if (d->coords) m->coords_host.assign(d->coords, d->coords + d->n_nodes * dim_of(d->elem_type));
+        if (d->mu && d->lambda) {
+            m->mu_host.assign(d->mu, d->mu + d->n_elems);
+            m->lam_host.assign(d->lambda, d->lambda + d->n_elems);
+        }
         std::vector<double> smu((size_t)d->n_nodes, 0.0), slam((size_t)d->n_nodes, 0.0), val((size_t)d->n_nodes, 0.0);
         for (int64_t e = 0; e < d->n_elems; ++e)
             for (int a = 0; a < ne_n; ++a) {
@@ -684,6 +693,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     femi::solver_free(m);
     femi::lp_mesh_free(m);
     femi::sparse_free(m);
+    femi::atomic_free(m);
     free_all(m);
     delete m;
     return FEM_OK;

@@ -13,6 +13,7 @@ namespace femi {
 struct SolverWork;  // Newton-CG workspace, created on first use (fem_solver.cu)
 struct LpMeshData;  // learned-preconditioner graph on the device (fem_learned.cu)
 struct SparseData;  // sparse-K pattern, colouring and workspace (fem_sparse.cu)
+struct AtomicData;  // element arrays of the atomic-scatter ablation (fem_atomic.cu)
 }
 
 struct fem_mesh {
@@ -57,6 +58,9 @@ struct fem_mesh {
     femi::LpMeshData* lp = nullptr;
     // sparse K by colouring (built by the first fem_sparse_* call)
     femi::SparseData* sparse = nullptr;
+    // host copies for the atomic-scatter ablation (natural element order)
+    std::vector<double> coords_host, mu_host, lam_host;
+    femi::AtomicData* atomic = nullptr;
 };
 
 namespace femi {
@@ -77,6 +81,11 @@ void solver_free(fem_mesh* m);
 void lp_mesh_free(fem_mesh* m);
 // frees the sparse-K data of `m` (no-op without it)
 void sparse_free(fem_mesh* m);
+// frees the atomic-ablation data of `m` (no-op without it)
+void atomic_free(fem_mesh* m);
+// P1 geometry of one element (vertices Xe [(D+1) * D]): grad N_a of the
+// first D vertices (the last one is the reference) and w det J
+void p1_geometry(int D, const double* Xe, double* out /* D * D + 1 */);
 // fills the CG preconditioner blocks Minv [n_nodes * 9] (FP32) from the
 // learned network `lp` at the FP32 state u: block diagonal, features,
 // network, SPD map (fem_learned.cu)

@@ -190,6 +190,25 @@ class Mesh:
         L.check(L.lib().fem_block_diag(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
         return out
 
+    # --- ablation: element-per-thread scatter with float atomics ---------------
+    def residual_atomic(self, u, mask_out=True, out=None, stream=None):
+        """fem_residual_atomic: the residual by atomic scatter-add (run-to-run
+        bit differences possible)."""
+        self._check_vec(u)
+        out = out if out is not None else torch.empty_like(u)
+        L.check(L.lib().fem_residual_atomic(self._h, _dtype_code(u), _ptr(u), _ptr(out),
+                                            L.FEM_MASK_OUT if mask_out else 0, _stream(stream)))
+        return out
+
+    def hvp_atomic(self, u, v, mask_in=True, mask_out=True, out=None, stream=None):
+        """fem_hvp_atomic: the HVP by atomic scatter-add."""
+        self._check_vec(u, v)
+        out = out if out is not None else torch.empty_like(u)
+        flags = (L.FEM_MASK_IN if mask_in else 0) | (L.FEM_MASK_OUT if mask_out else 0)
+        L.check(L.lib().fem_hvp_atomic(self._h, _dtype_code(u), _ptr(u), _ptr(v), _ptr(out), flags,
+                                       _stream(stream)))
+        return out
+
     # --- sparse K by colouring (Algorithm 2) ----------------------------------
     def sparse_info(self):
         """(nnz, n_colors) of K's DOF pattern and its distance-2 colouring
