@@ -68,16 +68,26 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def kernel_source_hash():
+# the sources that define what a residual or HVP call runs (tile and
+# finalize kernels, plan, records, launch); the solver, learned-
+# preconditioner, sparse and ablation sources do not change those kernels
+KERNEL_SOURCES = ("fem_api.cu", "fem_internal.h", "fem_kernels.cuh", "fem_material.cuh", "fem_plan.cpp",
+                  "fem_plan.h", "fem_vec.cuh")
+
+
+SPMV_SOURCES = ("fem_sparse.cu",)
+
+
+def kernel_source_hash(files=KERNEL_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_12365_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel_tag):
+def traffic_for(kernel_tag, files=KERNEL_SOURCES):
     """DRAM bytes per call from a committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", f"{kernel_tag}.traffic.json")
@@ -85,7 +95,7 @@ def traffic_for(kernel_tag):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash(files):
         return None
     return d.get("dram_bytes_per_call")
 
@@ -337,7 +347,8 @@ def sparse_arm(gm, ut, vt, t_hvp_us, flush_l2, peak):
             "spmv_us": t_spmv, "hvp_us": t_hvp_us, "spmv_vs_hvp_rel_err": rel,
             "spmv_roofline": {"bound": "hbm", "bytes": spmv_bytes, "achieved": spmv_bytes / (t_spmv * 1e-6) / 1e9,
                               "peak": peak, "unit": "GB/s",
-                              "frac": spmv_bytes / (t_spmv * 1e-6) / 1e9 / peak}}
+                              "frac": spmv_bytes / (t_spmv * 1e-6) / 1e9 / peak,
+                              "traffic": traffic_for("tet64_spmv_f32", SPMV_SOURCES)}}
 
 
 def atomic_arm(gm, ut, vt, t_res_us, t_hvp_us, flush_l2):
