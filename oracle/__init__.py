@@ -75,6 +75,13 @@ def lib():
         L.ora_lp_blocks.restype = i32
         L.ora_lp_blocks.argtypes = [i64, P, P, P, P]
         L.ora_lp_blocks_backward.argtypes = [i64, P, P, P, P, P]
+        L.ora_ncm_set.restype = i32
+        L.ora_ncm_set.argtypes = [i32, P]
+        L.ora_ncm_eval.argtypes = [dbl, dbl, P, P, P]
+        L.ora_law_psi.restype = dbl
+        L.ora_law_psi.argtypes = [i32, P, dbl, dbl]
+        L.ora_law_P.argtypes = [i32, P, dbl, dbl, P]
+        L.ora_law_dP.argtypes = [i32, P, P, dbl, dbl, P]
         L.ora_dof_pattern.restype = i64
         L.ora_dof_pattern.argtypes = [i64, i32, i64, i32, P, P, P, i64]
         L.ora_distance2_colors.restype = i32
@@ -318,3 +325,51 @@ def distance2_colors(ptr, idx):
     col = np.zeros(max(n, 1), np.int32)
     nc = lib().ora_distance2_colors(n, _p(ptr), _p(idx), _p(col))
     return col[:n], int(nc)
+
+
+# ----------------------------------------------------------------------------
+# neural constitutive model (process-wide switch of the oracle's law)
+# ----------------------------------------------------------------------------
+class ncm:
+    """Context manager: the oracle's element loops use psi = [NN(I1, J) -
+    NN(3, 1)] + psi_NH inside the block (params as ora_ncm_set)."""
+
+    def __init__(self, H, params):
+        self.H = int(H)
+        self.params = _f64(params)
+        assert self.params.size == self.H * self.H + 5 * self.H + 1
+
+    def __enter__(self):
+        lib().ora_ncm_set(self.H, _p(self.params))
+        return self
+
+    def __exit__(self, *a):
+        lib().ora_ncm_set(0, None)
+
+
+def ncm_eval(I1, J):
+    """(NN, gradient [2], Hessian [2, 2]) at (I1, J); needs an active ncm."""
+    y = C.c_double(0.0)
+    g = np.zeros(2)
+    h = np.zeros(4)
+    lib().ora_ncm_eval(float(I1), float(J), C.byref(y), _p(g), _p(h))
+    return y.value, g, h.reshape(2, 2)
+
+
+def law_psi(F, mu=1.0, lam=10.0):
+    F = _f64(F)
+    return lib().ora_law_psi(F.shape[0], _p(F), mu, lam)
+
+
+def law_P(F, mu=1.0, lam=10.0):
+    F = _f64(F)
+    P = np.zeros_like(F)
+    lib().ora_law_P(F.shape[0], _p(F), mu, lam, _p(P))
+    return P
+
+
+def law_dP(F, dF, mu=1.0, lam=10.0):
+    F, dF = _f64(F), _f64(dF)
+    dP = np.zeros_like(F)
+    lib().ora_law_dP(F.shape[0], _p(F), _p(dF), mu, lam, _p(dP))
+    return dP

@@ -118,6 +118,140 @@ void ora_nh_dP(int d, const double* F, const double* dF, double mu, double lam, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Neural constitutive model (Sec. "Neural Constitutive Modeling"):          */
+/*   psi = [NN(I1, J) - NN(3, 1)] + psi_NH(I1, J),                           */
+/* NN a two-hidden-layer softplus MLP of the invariants I1 = tr(F^T F) (+1   */
+/* in plane strain) and J = det F, shared by all elements; psi_NH the        */
+/* Neo-Hookean law above with the element's moduli (the convex base).        */
+/* Parameters: W1 [H][2], b1 [H], W2 [H][H] (W2[m][k]: unit k -> unit m),    */
+/* b2 [H], w3 [H], b3, as one array.  Set once; H = 0 restores pure NH.      */
+/* ------------------------------------------------------------------------ */
+static int ncm_h = 0;
+static double* ncm_w = NULL;
+static double ncm_nn0 = 0.0;
+
+static double sp_d(double t) { return t > 30.0 ? t : log1p(exp(t)); }
+static double sig_d(double t) { return 1.0 / (1.0 + exp(-t)); }
+
+/* NN value, gradient g[2] and Hessian h[4] (row-major) at (I1, J): the
+ * derivatives by the chain rule written forward, unit by unit:
+ * dz2_m/dx = sum_k W2[m][k] s(z1_k) W1[k][.],
+ * d2z2_m/dx dx' = sum_k W2[m][k] s'(z1_k) W1[k][.] W1[k][.]',
+ * dy/dx = sum_m w3_m s(z2_m) dz2_m/dx,
+ * d2y = sum_m w3_m (s'(z2_m) dz2_m dz2_m' + s(z2_m) d2z2_m). */
+void ora_ncm_eval(double I1, double J, double* y, double* g, double* h) {
+    const int H = ncm_h;
+    const double *W1 = ncm_w, *b1 = W1 + 2 * H, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H;
+    const double b3 = w3[H];
+    double out = b3, gg[2] = {0, 0}, hh[4] = {0, 0, 0, 0};
+    for (int m = 0; m < H; ++m) {
+        double z2 = b2[m], dz[2] = {0, 0}, d2z[4] = {0, 0, 0, 0};
+        for (int k = 0; k < H; ++k) {
+            const double z1 = W1[k * 2] * I1 + W1[k * 2 + 1] * J + b1[k];
+            const double s = sig_d(z1), ds = s * (1.0 - s);
+            const double w = W2[m * H + k];
+            z2 += w * sp_d(z1);
+            for (int a = 0; a < 2; ++a) {
+                dz[a] += w * s * W1[k * 2 + a];
+                for (int b = 0; b < 2; ++b) d2z[a * 2 + b] += w * ds * W1[k * 2 + a] * W1[k * 2 + b];
+            }
+        }
+        const double s2 = sig_d(z2), ds2 = s2 * (1.0 - s2);
+        out += w3[m] * sp_d(z2);
+        for (int a = 0; a < 2; ++a) {
+            gg[a] += w3[m] * s2 * dz[a];
+            for (int b = 0; b < 2; ++b) hh[a * 2 + b] += w3[m] * (ds2 * dz[a] * dz[b] + s2 * d2z[a * 2 + b]);
+        }
+    }
+    if (y) *y = out;
+    if (g) g[0] = gg[0], g[1] = gg[1];
+    if (h)
+        for (int k = 0; k < 4; ++k) h[k] = hh[k];
+}
+
+int ora_ncm_set(int H, const double* params) {
+    free(ncm_w);
+    ncm_w = NULL;
+    ncm_h = 0;
+    ncm_nn0 = 0.0;
+    if (H <= 0) return 0;
+    const size_t n = (size_t)H * H + 5 * (size_t)H + 1;
+    ncm_w = (double*)malloc(sizeof(double) * n);
+    memcpy(ncm_w, params, sizeof(double) * n);
+    ncm_h = H;
+    ora_ncm_eval(3.0, 1.0, &ncm_nn0, NULL, NULL);
+    return 0;
+}
+
+static double invariant_I1(int d, const double* F) {
+    double I1 = 0.0;
+    for (int k = 0; k < d * d; ++k) I1 += F[k] * F[k];
+    return d == 2 ? I1 + 1.0 : I1;
+}
+
+/* the law of the element loops: Neo-Hookean, plus the NN terms when set */
+static double law_psi(int d, const double* F, double mu, double lam) {
+    double psi = ora_nh_psi(d, F, mu, lam);
+    if (!ncm_h || !isfinite(psi)) return psi;
+    double y;
+    ora_ncm_eval(invariant_I1(d, F), det_d(d, F), &y, NULL, NULL);
+    return psi + (y - ncm_nn0);
+}
+
+/* roundoff scale of one point: the Neo-Hookean terms, plus |NN(I1, J)| and
+ * |NN(3, 1)| (the shift is a difference of those two) */
+static double law_term_scale(int d, const double* F, double mu, double lam) {
+    double s = nh_term_scale(d, F, mu, lam);
+    if (!ncm_h || !(det_d(d, F) > 0.0)) return s;
+    double y;
+    ora_ncm_eval(invariant_I1(d, F), det_d(d, F), &y, NULL, NULL);
+    return s + fabs(y) + fabs(ncm_nn0);
+}
+
+/* dpsi_NN/dF = 2 psi_I1 F + psi_J J F^-T */
+static void law_P(int d, const double* F, double mu, double lam, double* P) {
+    ora_nh_P(d, F, mu, lam, P);
+    if (!ncm_h) return;
+    double g[2], Fi[9], FiT[9];
+    const double J = det_d(d, F);
+    ora_ncm_eval(invariant_I1(d, F), J, NULL, g, NULL);
+    inv_d(d, F, Fi);
+    transpose_d(d, Fi, FiT);
+    for (int k = 0; k < d * d; ++k) P[k] += 2.0 * g[0] * F[k] + g[1] * J * FiT[k];
+}
+
+/* d(dpsi_NN/dF)[dF] = 2 psi_I1 dF + 2 F (h_11 dI1 + h_12 dJ)
+ *   + J F^-T (h_21 dI1 + h_22 dJ) + psi_J (dJ F^-T - J F^-T dF^T F^-T),
+ * dI1 = 2 F : dF, dJ = J tr(F^-1 dF) */
+static void law_dP(int d, const double* F, const double* dF, double mu, double lam, double* dP) {
+    ora_nh_dP(d, F, dF, mu, lam, dP);
+    if (!ncm_h) return;
+    double g[2], h[4], Fi[9] = {0}, FiT[9] = {0}, dFT[9] = {0}, T1[9] = {0}, T2[9] = {0}, A[9] = {0};
+    const double J = det_d(d, F);
+    ora_ncm_eval(invariant_I1(d, F), J, NULL, g, h);
+    inv_d(d, F, Fi);
+    transpose_d(d, Fi, FiT);
+    transpose_d(d, dF, dFT);
+    matmul_d(d, FiT, dFT, T1);
+    matmul_d(d, T1, FiT, T2);
+    matmul_d(d, Fi, dF, A);
+    double trA = 0.0, dI1 = 0.0;
+    for (int i = 0; i < d; ++i) trA += A[i * d + i];
+    for (int k = 0; k < d * d; ++k) dI1 += 2.0 * F[k] * dF[k];
+    const double dJ = J * trA;
+    const double a = h[0] * dI1 + h[1] * dJ, b = h[2] * dI1 + h[3] * dJ;
+    for (int k = 0; k < d * d; ++k)
+        dP[k] += 2.0 * g[0] * dF[k] + 2.0 * F[k] * a + J * FiT[k] * b + g[1] * (dJ * FiT[k] - J * T2[k]);
+}
+
+/* point-level law (NH, plus the NN terms when set), for the pins */
+double ora_law_psi(int d, const double* F, double mu, double lam) { return law_psi(d, F, mu, lam); }
+void ora_law_P(int d, const double* F, double mu, double lam, double* P) { law_P(d, F, mu, lam, P); }
+void ora_law_dP(int d, const double* F, const double* dF, double mu, double lam, double* dP) {
+    law_dP(d, F, dF, mu, lam, dP);
+}
+
+/* ------------------------------------------------------------------------ */
 /* isoparametric geometry (Eq. 2: w_q det J^e(xi_q); grad N = J^-T grad N^)  */
 /* ------------------------------------------------------------------------ */
 static const int HEXSGN[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
@@ -220,8 +354,8 @@ double ora_energy(int etype, int64_t n_nodes, int64_t n_el, const double* X,
         for (int q = 0; q < nq; ++q) {
             double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
             def_grad(d, ne, ue, gN, F);
-            pe += ora_nh_psi(d, F, mu[e], lam[e]) * wdJ;
-            asum += nh_term_scale(d, F, mu[e], lam[e]) * fabs(wdJ);
+            pe += law_psi(d, F, mu[e], lam[e]) * wdJ;
+            asum += law_term_scale(d, F, mu[e], lam[e]) * fabs(wdJ);
         }
         if (isinf(pe) && st == 0) st = 3;
         if (psi_e) psi_e[e] = pe;
@@ -258,7 +392,7 @@ void ora_residual(int etype, int64_t n_nodes, int64_t n_el, const double* X,
             double wdJ = ora_geometry(etype, Xe, q, gN, NULL);
             def_grad(d, ne, ue, gN, F);
             if (!(det_d(d, F) > 0.0) && st == 0) st = 3;
-            ora_nh_P(d, F, mu[e], lam[e], P);
+            law_P(d, F, mu[e], lam[e], P);
             for (int a = 0; a < ne; ++a)
                 for (int i = 0; i < d; ++i) {
                     double s = 0.0;
@@ -298,7 +432,7 @@ void ora_hvp(int etype, int64_t n_nodes, int64_t n_el, const double* X,
             def_grad(d, ne, ue, gN, F);
             if (!(det_d(d, F) > 0.0) && st == 0) st = 3;
             grad_field(d, ne, ve, gN, dF);
-            ora_nh_dP(d, F, dF, mu[e], lam[e], dP);
+            law_dP(d, F, dF, mu[e], lam[e], dP);
             for (int a = 0; a < ne; ++a)
                 for (int i = 0; i < d; ++i) {
                     double s = 0.0;
@@ -338,7 +472,7 @@ void ora_block_diag(int etype, int64_t n_nodes, int64_t n_el, const double* X,
                     /* dF = e_k (x) gradN_a */
                     for (int i = 0; i < d; ++i)
                         for (int j = 0; j < d; ++j) dF[i * d + j] = (i == k) ? gN[a * d + j] : 0.0;
-                    ora_nh_dP(d, F, dF, mu[e], lam[e], dP);
+                    law_dP(d, F, dF, mu[e], lam[e], dP);
                     for (int i = 0; i < d; ++i) {
                         double s = 0.0;
                         for (int j = 0; j < d; ++j) s += dP[i * d + j] * gN[a * d + j];

@@ -140,6 +140,21 @@ int ora_lp_blocks(int64_t nn, const double* D, const uint8_t* mask, const double
 void ora_lp_blocks_backward(int64_t nn, const double* D, const uint8_t* mask, const double* o,
                             const double* gM, double* go);
 
+/* Neural constitutive model (Sec. "Neural Constitutive Modeling"):
+ *   psi = [NN(I1, J) - NN(3, 1)] + psi_NH,
+ * NN: 2 -> H -> H -> 1 MLP, softplus activations, of I1 = tr(F^T F) (+1 in
+ * plane strain) and J = det F.  params (H*H + 5H + 1 doubles): W1 [H][2],
+ * b1 [H], W2 [H][H] (row m: unit m of layer 2), b2 [H], w3 [H], b3.
+ * ora_ncm_set installs it for every element loop (energy, residual, HVP,
+ * block diagonal, load step); H = 0 restores the Neo-Hookean law alone. */
+int ora_ncm_set(int H, const double* params);
+/* NN value, gradient [2] and Hessian [2][2] in (I1, J) (each nullable). */
+void ora_ncm_eval(double I1, double J, double* y, double* g, double* h);
+/* the point-level law as the element loops use it */
+double ora_law_psi(int d, const double* F, double mu, double lam);
+void ora_law_P(int d, const double* F, double mu, double lam, double* P);
+void ora_law_dP(int d, const double* F, const double* dF, double mu, double lam, double* dP);
+
 /* Sparse K by colouring (Sec. 2.2, Algorithm 2; App. A, B).
  * DOF pattern (App. B): CSR over DOFs (dof = node*dim + component), entry
  * (i, j) when the nodes of i and j share an element (the node itself

@@ -295,6 +295,20 @@ def workload_hex(n: int = 128, seed: int = 0) -> Mesh:
     return bc_base_and_top_3d(m, (0.1, 0.0, 0.0))
 
 
+def ncm_params(H: int = 16, seed: int = 0, amp: float = 0.2) -> np.ndarray:
+    """Synthetic (untrained) weights of the neural constitutive model's MLP
+    2 -> H -> H -> 1: W1 [H][2], b1, W2 [H][H], b2, w3, b3 flattened, all
+    from the seeded normal stream; `amp` scales the output layer."""
+    z = normal(seed, 11, H * H + 5 * H + 1)
+    W1 = z[:2 * H]
+    b1 = 0.5 * z[2 * H:3 * H]
+    W2 = z[3 * H:3 * H + H * H] / np.sqrt(H)
+    b2 = 0.5 * z[3 * H + H * H:4 * H + H * H]
+    w3 = amp * z[4 * H + H * H:5 * H + H * H] / np.sqrt(H)
+    b3 = z[5 * H + H * H:]
+    return np.concatenate([W1, b1, W2, b2, w3, b3]).astype(np.float64)
+
+
 def smooth_state(mesh: Mesh, s: float, amp: float = 0.02) -> np.ndarray:
     """BC-consistent displacement at load factor s: the affine interpolant of
     the prescribed data plus ``amp * prod_k sin(2 pi x_k)`` in every component
