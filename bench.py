@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cells", dest="n", type=int, default=64, help="cells per side of the tet workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ncm", action="store_true", help="skip the neural-constitutive-model measurement")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the sparse-K (Algorithm 2) and atomic-scatter ablation measurements")
     ap.add_argument("--newton-steps", type=int, default=2,
@@ -382,6 +383,61 @@ def atomic_arm(gm, ut, vt, t_res_us, t_hvp_us, flush_l2):
             "hvp_entries_differing_between_two_runs": int((y2 != y).sum()), "n_dofs": gm.n_dofs}
 
 
+NCM_H = 32
+
+
+def ncm_arm(m, gm, ut, vt, t_res_us, t_hvp_us, flush_l2, dev):
+    """The neural constitutive model (psi = [NN(I1, J) - NN(3, 1)] + psi_NH,
+    a 2 -> 32 -> 32 -> 1 softplus MLP with synthetic weights) on the
+    benchmark mesh: residual and HVP calls (each evaluates the network at
+    every element first), and one mixed-precision Newton load step of the
+    random-moduli mesh with and without the network."""
+    import torch
+    from paper_2602_12365_b300 import meshgen as mg
+    from paper_2602_12365_b300.fem import Mesh
+
+    def timed(fn, reps=20):
+        ts = []
+        for k in range(reps):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(ts)
+
+    p = mg.ncm_params(NCM_H, seed=7, amp=0.2)
+    gm.set_ncm(NCM_H, p)
+    r, y = torch.empty_like(ut), torch.empty_like(ut)
+    gm.residual(ut, out=r)
+    t_r = timed(lambda: gm.residual(ut, out=r))
+    t_h = timed(lambda: gm.hvp(ut, vt, out=y))
+    gm.set_ncm(0)
+    mn = mg.workload_tet(m.n, seed=101, random_moduli=101)
+    gn = Mesh.from_fixture(mn, precision="mixed")
+    ubar = torch.as_tensor(mn.ubar.ravel(), dtype=torch.float64, device=dev)
+    out = {}
+    for arm, net in (("neo_hookean", False), ("ncm", True)):
+        gn.set_ncm(NCM_H, p) if net else gn.set_ncm(0)
+        u = torch.zeros(mn.n_nodes * 3, dtype=torch.float64, device=dev)
+        gn.newton_step(u, ubar, 0.0, 0.0, cg_dtype=torch.float32)  # workspace
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        st = gn.newton_step(u, ubar, 0.0, 0.05, cg_dtype=torch.float32)
+        b.record()
+        b.synchronize()
+        out[arm] = {"s": a.elapsed_time(b) * 1e-3, "newton_iters": st["newton_iters"], "cg_iters": st["cg_iters"],
+                    "status": st["status"]}
+    return {"what": f"psi = [NN(I1, J) - NN(3, 1)] + psi_NH, NN 2 -> {NCM_H} -> {NCM_H} -> 1 softplus MLP "
+                    "(synthetic weights, seed 7), FP32 kernels; each residual / HVP call evaluates the "
+                    "network at every element first (the Newton PCG once per solve)",
+            "residual_us": t_r, "hvp_us": t_h, "neo_hookean_residual_us": t_res_us,
+            "neo_hookean_hvp_us": t_hvp_us, "newton_first_load_step_mixed": out}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_init(args)
@@ -517,6 +573,8 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
+    if not args.no_ncm and rank == 0:
+        line["ncm"] = ncm_arm(m, gm, ut, vt, t_res * 1e3, t_hvp * 1e3, flush_l2, dev)
     if not args.no_sparse and rank == 0:  # per-GPU measurements, reported by rank 0
         line["atomic_ablation"] = atomic_arm(gm, ut, vt, t_res * 1e3, t_hvp * 1e3, flush_l2)
         line["sparse"] = sparse_arm(gm, ut, vt, t_hvp * 1e3, flush_l2, peak)

@@ -390,6 +390,30 @@ fem_status fem_lp_train_step(fem_lp* lp, fem_mesh* mesh, const float* u, const f
                              double* loss, void* stream);
 
 /*
+ * fem_mesh_set_ncm -- the neural constitutive model (Sec. "Neural
+ * Constitutive Modeling"): from this call on, the element operators of the
+ * mesh (fem_energy, fem_energy_static, fem_residual, fem_hvp,
+ * fem_block_diag, and through them fem_newton_step, fem_tangent_solve and
+ * fem_sparse_assemble) evaluate
+ *   psi = [NN(I1, J) - NN(3, 1)] + psi_NH(mu_e, lambda_e),
+ * NN a 2 -> H -> H -> 1 MLP with softplus activations of the invariants
+ * I1 = tr(F^T F) (+1 in plane strain) and J = det F, the same for every
+ * element; the Neo-Hookean law with the element's moduli is the convex base.
+ *   hidden  H = 8, 16 or 32; 0 removes the network (Neo-Hookean again).
+ *   params  HOST double [H*H + 5H + 1]: W1 [H][2], b1 [H], W2 [H][H] (row m
+ *           feeds unit m of the second layer), b2 [H], w3 [H], b3; copied.
+ * Each operator call first evaluates the network at every element's (I1, J)
+ * (an invariants pass of the element kernel and a network kernel, in the
+ * call's precision); the PCG of the Newton solver evaluates it once per
+ * solve.  The network does not depend on the moduli, so fem_param_vjp is
+ * unchanged.  The arrays (8 + 2 values per element and precision) are
+ * allocated here, so the operator calls allocate nothing.  P1 meshes only
+ * (FEM_ERR_ARG for hexahedra); the atomic-scatter ablation refuses a mesh
+ * with a network.  Synchronises the device.
+ */
+fem_status fem_mesh_set_ncm(fem_mesh* mesh, int hidden, const double* params);
+
+/*
  * Sparse K by colouring -- the paper's second route to the tangent (Sec. 2.2,
  * Algorithm 2; App. A for the colouring, App. B for the pattern).
  *

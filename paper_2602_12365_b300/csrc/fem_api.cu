@@ -234,7 +234,23 @@ KFn pick(int op) {
     }
 }
 
-KFn kernel_for(int et, int dtype, int op) {
+// the neural constitutive model's kernels (P1 only)
+template <int ET, typename T>
+KFn pick_ncm(int op) {
+    switch (op) {
+        case fem::OP_ENERGY: return fem::tile_kernel<ET, T, fem::OP_ENERGY, true>;
+        case fem::OP_RESIDUAL: return fem::tile_kernel<ET, T, fem::OP_RESIDUAL, true>;
+        case fem::OP_HVP: return fem::tile_kernel<ET, T, fem::OP_HVP, true>;
+        case fem::OP_BLOCKDIAG: return fem::tile_kernel<ET, T, fem::OP_BLOCKDIAG, true>;
+        default: return fem::tile_kernel<ET, T, fem::OP_NCM_INV>;
+    }
+}
+
+KFn kernel_for(int et, int dtype, int op, bool ncm) {
+    if (ncm || op == fem::OP_NCM_INV) {
+        if (dtype == FEM_F64) return et == 0 ? pick_ncm<0, double>(op) : pick_ncm<1, double>(op);
+        return et == 0 ? pick_ncm<0, float>(op) : pick_ncm<1, float>(op);
+    }
     if (dtype == FEM_F64) {
         if (et == 0) return pick<0, double>(op);
         if (et == 1) return pick<1, double>(op);
@@ -336,6 +352,20 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");
     const int pi = dtype == FEM_F64 ? 0 : 1;
     const int tsize = dtype == FEM_F64 ? 8 : 4;
+    // neural constitutive model: the network's coefficients at u (invariants
+    // pass, then the network), unless the caller knows they are current
+    const bool ncm = m->ncm != nullptr &&
+                     (op == fem::OP_ENERGY || op == fem::OP_RESIDUAL || op == fem::OP_HVP || op == fem::OP_BLOCKDIAG);
+    if (ncm && !(flags & femi::kFlagNcmCurrent)) {
+        fem_status s = femi::ncm_prepare(m, dtype, st);
+        if (s == FEM_OK)
+            s = launch(m, dtype, fem::OP_NCM_INV, u, nullptr, nullptr, nullptr, nullptr, nullptr, 0, st, nullptr, skip,
+                       0);
+        const int mode = op == fem::OP_ENERGY ? 0 : (op == fem::OP_RESIDUAL ? 1 : 2);
+        if (s == FEM_OK) s = femi::ncm_coefficients(m, dtype, mode, st, skip);
+        if (s != FEM_OK) return s;
+    }
+    flags &= ~femi::kFlagNcmCurrent;
     fem::KParams p{};
     p.tile_round_ptr = m->tile_round_ptr;
     p.tile_node_ptr = m->tile_node_ptr;
@@ -366,6 +396,10 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.status = m->status;
     p.skip = skip;
     p.vkv_tiles = vkv_tiles;
+    if (m->ncm) {
+        p.ncm_coef = femi::ncm_coef(m, pi);
+        p.ncm_inv = femi::ncm_inv(m, pi);
+    }
     p.u = u;
     p.v = v;
     p.out = out;
@@ -374,7 +408,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_lam = out_lam;
     p.flags = flags;
     const int smem = fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi]).total;
-    KFn fn = kernel_for(m->etype, dtype, op);
+    KFn fn = kernel_for(m->etype, dtype, op, ncm);
     int grid = 0;
     {
         // raise the dynamic shared-memory limit once per (device, kernel)
@@ -694,6 +728,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     femi::lp_mesh_free(m);
     femi::sparse_free(m);
     femi::atomic_free(m);
+    femi::ncm_free(m);
     free_all(m);
     delete m;
     return FEM_OK;

@@ -209,6 +209,7 @@ fem_status dispatch(fem_mesh* m, int dtype, int op, const void* u, const void* v
                     void* stream) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (m->etype == FEM_HEX8) return fail(FEM_ERR_ARG, "the atomic-scatter ablation covers P1 elements only");
+    if (m->ncm) return fail(FEM_ERR_ARG, "the atomic-scatter ablation evaluates the Neo-Hookean law only");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
     if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
         return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");

@@ -14,6 +14,7 @@ struct SolverWork;  // Newton-CG workspace, created on first use (fem_solver.cu)
 struct LpMeshData;  // learned-preconditioner graph on the device (fem_learned.cu)
 struct SparseData;  // sparse-K pattern, colouring and workspace (fem_sparse.cu)
 struct AtomicData;  // element arrays of the atomic-scatter ablation (fem_atomic.cu)
+struct NcmData;     // neural constitutive model: network and per-element arrays (fem_ncm.cu)
 }
 
 struct fem_mesh {
@@ -61,6 +62,8 @@ struct fem_mesh {
     // host copies for the atomic-scatter ablation (natural element order)
     std::vector<double> coords_host, mu_host, lam_host;
     femi::AtomicData* atomic = nullptr;
+    // neural constitutive model (set by fem_mesh_set_ncm; null: Neo-Hookean)
+    femi::NcmData* ncm = nullptr;
 };
 
 namespace femi {
@@ -83,6 +86,18 @@ void lp_mesh_free(fem_mesh* m);
 void sparse_free(fem_mesh* m);
 // frees the atomic-ablation data of `m` (no-op without it)
 void atomic_free(fem_mesh* m);
+// neural constitutive model (fem_ncm.cu).  An internal flag of run_op /
+// launch: the network's coefficients are current for this u and dtype (a
+// PCG solve at a fixed state), so the coefficient pass is skipped.
+constexpr unsigned kFlagNcmCurrent = 1u << 16;
+void ncm_free(fem_mesh* m);
+// allocates the per-element arrays of `dtype` on first use
+fem_status ncm_prepare(fem_mesh* m, int dtype, cudaStream_t st);
+// the network on every element's invariants: coefficients in record order
+// (mode 0: value and scale, 1: also the gradient, 2: also the Hessian)
+fem_status ncm_coefficients(fem_mesh* m, int dtype, int mode, cudaStream_t st, const int* skip);
+const void* ncm_coef(const fem_mesh* m, int pi);
+void* ncm_inv(const fem_mesh* m, int pi);
 // P1 geometry of one element (vertices Xe [(D+1) * D]): grad N_a of the
 // first D vertices (the last one is the reference) and w det J
 void p1_geometry(int D, const double* Xe, double* out /* D * D + 1 */);

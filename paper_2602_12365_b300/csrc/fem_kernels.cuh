@@ -55,7 +55,9 @@ constexpr int kStages = FEM_RING_STAGES;  // ring stages per warp
 constexpr int kSpinLimit = 1 << 20;  // bounded mbarrier waits
 constexpr int kFinThreads = 256;
 
-enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4 };
+// OP_NCM_INV writes each P1 element's (I1 - 3, J - 1) in record order: the
+// inputs of the neural constitutive model's network (coefficient pass)
+enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4, OP_NCM_INV = 5 };
 
 template <int ET>
 struct ElemT;
@@ -171,6 +173,11 @@ struct KParams {
     int* status;
     const int* skip;  // device flag: the call does nothing when *skip != 0 (may be null)
     int vkv_tiles;    // HVP: write the per-tile vKv partials (tile_red) even without out_scalar
+    // neural constitutive model, in record order (round * 32 + lane): the
+    // network's coefficients [8] per element (NCM kernels) and the invariants
+    // [2] per element (OP_NCM_INV)
+    const void* ncm_coef;
+    void* ncm_inv;
     // call
     const void* u;
     const void* v;
@@ -494,15 +501,33 @@ __device__ __forceinline__ void outer_sum(const V (*du)[D], const V (*g)[D], int
 // and the moduli, accumulate contributions f[a] for those nodes (f[NM1] is the
 // reference node for the block diagonal) and the scalar sums.  `valid` has a
 // bit per lane-vector component that holds a real element.
-template <int OP, int D, int NM1, class V>
+// Per-element coefficients of the neural constitutive model (unscaled):
+// the shifted network value, its roundoff scale, and NcmCoef's derivatives
+template <int D, class V>
+struct NcmElem {
+    V C0, Cs;
+    NcmCoef<D, V> d;
+};
+
+template <int OP, int D, int NM1, class V, bool NCM = false>
 __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D], const V (&g)[NM1][D],
                                         V wdJ, V mu, V lam, int valid, V (&f)[NM1 + 1][6],
                                         ScalarAcc<typename VT<V>::S>& acc, bool scal, double (&gmu)[2],
-                                        double (&glam)[2], int& inv) {
+                                        double (&glam)[2], int& inv, const NcmElem<D, V>* ncm = nullptr,
+                                        typename VT<V>::S* ninv = nullptr) {
     using S = typename VT<V>::S;
     constexpr int N = VT<V>::N;
+    static_assert(!NCM || N == 1, "the neural constitutive model runs one element per lane");
     Kin<D, V> k;
     kinematics<D, V>(H, k);
+    if constexpr (OP == OP_NCM_INV) {
+        static_assert(N == 1, "scalar lanes");
+        if (valid & 1) {
+            ninv[0] = vfma(splat<V>(S(2)), k.trH, k.HH);  // I1 - 3 = 2 tr H + H : H
+            ninv[1] = k.Jm1;
+        }
+        return;
+    }
     const int bad = valid & ~k.ok;
     if (bad) {
         inv |= bad;
@@ -510,9 +535,22 @@ __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D],
     }
     const int good = valid & k.ok;
     wdJ = vsel(good, wdJ, S(0));  // inverted or empty halves contribute nothing
+    // the network's coefficients scaled by w det J (zero for bad lanes)
+    NcmCoef<D, V> nc{};
+    if constexpr (NCM) {
+        nc.C2 = wdJ * ncm->d.C2;
+        nc.C3 = wdJ * ncm->d.C3;
+        nc.C11 = wdJ * ncm->d.C11;
+        nc.C12 = wdJ * ncm->d.C12;
+        nc.C22 = wdJ * ncm->d.C22;
+    }
     if constexpr (OP == OP_ENERGY) {
         V psi, sc;
         density<D, V>(k, mu, lam, psi, sc);
+        if constexpr (NCM) {
+            psi = psi + ncm->C0;
+            sc = sc + ncm->Cs;
+        }
         // select, not multiply: a lane without an element (degenerate Q1
         // geometry) may carry a non-finite density
         const V a = vsel(good, wdJ * psi, S(0)), b = vsel(good, wdJ * sc, S(0));
@@ -526,9 +564,15 @@ __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D],
         const V wmu = wdJ * mu, wlam = wdJ * lam;
         V P[D][D];
         if constexpr (OP == OP_RESIDUAL) {
-            stress<D, V>(H, k, wmu, wlam, P);
+            if constexpr (NCM)
+                stress_ncm<D, V>(H, k, wmu, wlam, nc, P);
+            else
+                stress<D, V>(H, k, wmu, wlam, P);
         } else {
-            tangent<D, V>(dF, k, wmu, wlam, P);
+            if constexpr (NCM)
+                tangent_ncm<D, V>(H, dF, k, wmu, wlam, nc, P);
+            else
+                tangent<D, V>(dF, k, wmu, wlam, P);
             if (scal) {  // w detJ dP : dF
                 V e = P[0][0] * dF[0][0];
 #pragma unroll
@@ -592,6 +636,7 @@ __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D],
                 f[a][1] = f[a][1] + vfma(c * gp[1], gp[1], mn);
                 f[a][2] = vfma(c * gp[0], gp[1], f[a][2]);
             }
+            if constexpr (NCM) block_ncm<D, V>(H, k, g0, gp, nc, f[a]);
         }
     } else if constexpr (OP == OP_PVJP) {
         // dP/dmu : grad a = (H - G) : grad a ; dP/dlam : grad a = lnJ (I + G) : grad a
@@ -627,10 +672,11 @@ struct Packer<2, ET, T> {
 };
 
 // element of a round pair / single: gather, compute, return contributions
-template <int ET, typename T, int OP, class V>
+template <int ET, typename T, int OP, class V, bool NCM = false>
 __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, const T* sU, const T* sV,
                                              const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc<T>& acc,
-                                             bool scal, double (&gmu)[2], double (&glam)[2], int& inv) {
+                                             bool scal, double (&gmu)[2], double (&glam)[2], int& inv,
+                                             const NcmElem<ElemT<ET>::D, V>* ncm = nullptr, T* ninv = nullptr) {
     using E = ElemT<ET>;
     using S = typename VT<V>::S;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1, NG = E::NG;
@@ -700,7 +746,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
         for (int a = 0; a <= NM1; ++a)
 #pragma unroll
             for (int c = 0; c < 6; ++c) fq[a][c] = splat<V>(S(0));
-        qp_work<OP, D, NM1, V>(H, dF, g, wdJ, mu, lam, valid, fq, acc, scal, gmu, glam, inv);
+        qp_work<OP, D, NM1, V, NCM>(H, dF, g, wdJ, mu, lam, valid, fq, acc, scal, gmu, glam, inv, ncm, ninv);
         if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -720,6 +766,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
                 for (int c = 0; c < 6; ++c) f[a][c] = fq[a][c];
         }
     } else {
+        static_assert(!NCM && OP != OP_NCM_INV, "the neural constitutive model covers P1 elements");
         // Q1: reference node 0; J rebuilt at each Gauss point
         V dx[NM1][D], du[NM1][D], dv[NM1][D];
         {
@@ -918,12 +965,13 @@ __device__ __forceinline__ void reduce_tiles(const double* tile_red, int n_tiles
 // ---------------------------------------------------------------------------
 constexpr int kEmptyLane = 0xFFFF;  // local id of an empty lane (the planner's kNoNode)
 
-template <int ET, typename T, int OP>
+// NCM: the neural constitutive model's terms from p.ncm_coef (P1 only)
+template <int ET, typename T, int OP, bool NCM = false>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     using E = ElemT<ET>;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW;
     constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP);
-    constexpr bool kPacked = (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4);
+    constexpr bool kPacked = (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4 && !NCM && OP != OP_NCM_INV);
     using V = typename std::conditional<kPacked, F2, T>::type;
     constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
@@ -1166,9 +1214,33 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                 // compute on zero geometry and skip the scatter
 #pragma unroll
                 for (int h = 0; h < NR; ++h)
-                    if (k0 + h < my_n)
-                        element_work<ET, T, OP, V>(&hs[h], (valid >> h) & 1, sU, sV, sX, f[NF == 1 ? 0 : h], acc,
-                                                   want_scalar, gmu[h], glam[h], inv);
+                    if (k0 + h < my_n) {
+                        // this lane's element in record order (round * 32 + lane)
+                        const int64_t rec = (int64_t)(my_r0 + k0 + h) * 32 + lane;
+                        NcmElem<D, V> ne{};
+                        if constexpr (NCM) {
+                            T c[8];
+                            const T* src = static_cast<const T*>(p.ncm_coef) + rec * 8;
+                            if constexpr (sizeof(T) == 4) {
+                                const float4 c0 = __ldg(reinterpret_cast<const float4*>(src));
+                                const float4 c1 = __ldg(reinterpret_cast<const float4*>(src) + 1);
+                                c[0] = c0.x, c[1] = c0.y, c[2] = c0.z, c[3] = c0.w;
+                                c[4] = c1.x, c[5] = c1.y, c[6] = c1.z, c[7] = c1.w;
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const double2 cj = __ldg(reinterpret_cast<const double2*>(src) + j);
+                                    c[2 * j] = cj.x, c[2 * j + 1] = cj.y;
+                                }
+                            }
+                            ne.C0 = c[0], ne.Cs = c[1];
+                            ne.d.C2 = c[2], ne.d.C3 = c[3], ne.d.C11 = c[4], ne.d.C12 = c[5], ne.d.C22 = c[6];
+                        }
+                        T* ninv = nullptr;
+                        if constexpr (OP == OP_NCM_INV) ninv = static_cast<T*>(p.ncm_inv) + rec * 2;
+                        element_work<ET, T, OP, V, NCM>(&hs[h], (valid >> h) & 1, sU, sV, sX, f[NF == 1 ? 0 : h],
+                                                        acc, want_scalar, gmu[h], glam[h], inv, &ne, ninv);
+                    }
             }
             if constexpr (OP == OP_PVJP) {
 #pragma unroll

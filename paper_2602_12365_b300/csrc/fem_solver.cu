@@ -957,8 +957,11 @@ private:
         // w = K z with z . K z (fused), then the update
         // (both as programmatic dependent launches: each kernel's blocks are
         // placed while the previous kernel drains)
-        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr, FEM_MASK_IN | FEM_MASK_OUT,
-                             st_, &w->cg->done, /*vkv_tiles=*/1));
+        // (a neural constitutive model's coefficients at ucg are current: the
+        // preconditioner build evaluated them, and the state is fixed)
+        FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr,
+                             FEM_MASK_IN | FEM_MASK_OUT | femi::kFlagNcmCurrent, st_, &w->cg->done,
+                             /*vkv_tiles=*/1));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)cg_grid<D, T>());
         cfg.blockDim = dim3(kVT);

@@ -190,6 +190,18 @@ class Mesh:
         L.check(L.lib().fem_block_diag(self._h, _dtype_code(u), _ptr(u), _ptr(out), _stream(stream)))
         return out
 
+    # --- neural constitutive model -------------------------------------------
+    def set_ncm(self, hidden: int, params=None):
+        """psi = [NN(I1, J) - NN(3, 1)] + psi_NH for every operator of this
+        mesh (fem_mesh_set_ncm); hidden = 0 restores the Neo-Hookean law."""
+        if hidden == 0:
+            L.check(L.lib().fem_mesh_set_ncm(self._h, 0, None))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        if p.size != hidden * hidden + 5 * hidden + 1:
+            raise ValueError("params must hold H*H + 5H + 1 values")
+        L.check(L.lib().fem_mesh_set_ncm(self._h, int(hidden), p.ctypes.data_as(C.c_void_p)))
+
     # --- ablation: element-per-thread scatter with float atomics ---------------
     def residual_atomic(self, u, mask_out=True, out=None, stream=None):
         """fem_residual_atomic: the residual by atomic scatter-add (run-to-run
