@@ -512,13 +512,32 @@ def run_ours(args):
         ud = torch.empty_like(ut)
         vd = torch.empty_like(ut)
 
+        # copies on their own streams: v goes up while the residual runs, r
+        # comes down while the HVP runs (the two directions overlap)
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        ev = {k: torch.cuda.Event() for k in ("go", "u", "v", "r", "y", "rh", "yh")}
+
         def e2e_step():
-            ud.copy_(uh, non_blocking=True)
-            vd.copy_(vh, non_blocking=True)
-            gm.residual(ud, out=r)
-            gm.hvp(ud, vd, out=y)
-            rh.copy_(r, non_blocking=True)
-            yh.copy_(y, non_blocking=True)
+            ev["go"].record(stream)
+            s_in.wait_event(ev["go"])
+            with torch.cuda.stream(s_in):
+                ud.copy_(uh, non_blocking=True)
+                ev["u"].record(s_in)
+                vd.copy_(vh, non_blocking=True)
+                ev["v"].record(s_in)
+            stream.wait_event(ev["u"])
+            gm.residual(ud, out=r, stream=stream)
+            ev["r"].record(stream)
+            stream.wait_event(ev["v"])
+            gm.hvp(ud, vd, out=y, stream=stream)
+            ev["y"].record(stream)
+            s_out.wait_event(ev["r"])
+            with torch.cuda.stream(s_out):
+                rh.copy_(r, non_blocking=True)
+                s_out.wait_event(ev["y"])
+                yh.copy_(y, non_blocking=True)
+                ev["yh"].record(s_out)
+            stream.wait_event(ev["yh"])  # the step ends when y is on the host
 
         for k in range(3):
             flush_l2(k)
