@@ -246,7 +246,18 @@ KFn pick_ncm(int op) {
     }
 }
 
-KFn kernel_for(int et, int dtype, int op, bool ncm) {
+KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
+    if (lin) {
+        if (dtype == FEM_F64)
+            return et == 0 ? fem::tile_kernel<0, double, fem::OP_HVP, false, true>
+                           : fem::tile_kernel<1, double, fem::OP_HVP, false, true>;
+        return et == 0 ? fem::tile_kernel_lin<0> : fem::tile_kernel_lin<1>;
+    }
+    if (op == fem::OP_LINEARIZE) {
+        if (dtype == FEM_F64)
+            return et == 0 ? fem::tile_kernel<0, double, fem::OP_LINEARIZE> : fem::tile_kernel<1, double, fem::OP_LINEARIZE>;
+        return et == 0 ? fem::tile_kernel<0, float, fem::OP_LINEARIZE> : fem::tile_kernel<1, float, fem::OP_LINEARIZE>;
+    }
     if (ncm || op == fem::OP_NCM_INV) {
         if (dtype == FEM_F64) return et == 0 ? pick_ncm<0, double>(op) : pick_ncm<1, double>(op);
         return et == 0 ? pick_ncm<0, float>(op) : pick_ncm<1, float>(op);
@@ -288,6 +299,10 @@ int worst_smem(int et, int nlp, bool mixed, bool mat) {
     for (int op = 0; op < 5; ++op) {
         w = std::max(w, fem::smem_layout(et, 8, op, nlp, record_bytes(et, mat, 8)).total);
         if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nlp, record_bytes(et, mat, 4)).total);
+    }
+    if (et != 2) {  // the HVP from a stored linearisation
+        w = std::max(w, fem::smem_layout(et, 8, fem::OP_HVP, nlp, record_bytes(et, mat, 8), true).total);
+        if (mixed) w = std::max(w, fem::smem_layout(et, 4, fem::OP_HVP, nlp, record_bytes(et, mat, 4), true).total);
     }
     return w;
 }
@@ -366,6 +381,20 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         if (s != FEM_OK) return s;
     }
     flags &= ~femi::kFlagNcmCurrent;
+    // the stored linearisation: written by OP_LINEARIZE, read by an HVP that
+    // asks for it (P1, Neo-Hookean)
+    const bool lin = op == fem::OP_HVP && (flags & femi::kFlagUseLin) && !ncm && m->etype != 2;
+    flags &= ~femi::kFlagUseLin;
+    if (op == fem::OP_LINEARIZE) {
+        if (m->etype == 2 || m->ncm) return fail(FEM_ERR_ARG, "the stored linearisation covers Neo-Hookean P1 meshes");
+        if (!m->lin[pi]) {
+            void* q = nullptr;
+            fem_status s = zalloc(m, &q, (size_t)m->plan.n_rounds() * 32 * fem::kLinVals * tsize, st);
+            if (s != FEM_OK) return s;
+            m->lin[pi] = q;
+        }
+    }
+    if (lin && !m->lin[pi]) return fail(FEM_ERR_ARG, "HVP from a linearisation that was never stored");
     fem::KParams p{};
     p.tile_round_ptr = m->tile_round_ptr;
     p.tile_node_ptr = m->tile_node_ptr;
@@ -400,6 +429,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         p.ncm_coef = femi::ncm_coef(m, pi);
         p.ncm_inv = femi::ncm_inv(m, pi);
     }
+    p.lin = m->lin[pi];
     p.u = u;
     p.v = v;
     p.out = out;
@@ -407,8 +437,8 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_mu = out_mu;
     p.out_lam = out_lam;
     p.flags = flags;
-    const int smem = fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi]).total;
-    KFn fn = kernel_for(m->etype, dtype, op, ncm);
+    const int smem = fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi], lin).total;
+    KFn fn = kernel_for(m->etype, dtype, op, ncm, lin);
     int grid = 0;
     {
         // raise the dynamic shared-memory limit once per (device, kernel)

@@ -64,6 +64,8 @@ struct fem_mesh {
     femi::AtomicData* atomic = nullptr;
     // neural constitutive model (set by fem_mesh_set_ncm; null: Neo-Hookean)
     femi::NcmData* ncm = nullptr;
+    // stored linearisation per precision (OP_LINEARIZE; allocated on first use)
+    void* lin[2] = {nullptr, nullptr};
 };
 
 namespace femi {
@@ -90,6 +92,9 @@ void atomic_free(fem_mesh* m);
 // launch: the network's coefficients are current for this u and dtype (a
 // PCG solve at a fixed state), so the coefficient pass is skipped.
 constexpr unsigned kFlagNcmCurrent = 1u << 16;
+// internal flag: an HVP at the state of the last OP_LINEARIZE call in this
+// precision (Neo-Hookean P1 meshes): it reads the stored linearisation
+constexpr unsigned kFlagUseLin = 1u << 17;
 void ncm_free(fem_mesh* m);
 // allocates the per-element arrays of `dtype` on first use
 fem_status ncm_prepare(fem_mesh* m, int dtype, cudaStream_t st);

@@ -57,7 +57,12 @@ constexpr int kFinThreads = 256;
 
 // OP_NCM_INV writes each P1 element's (I1 - 3, J - 1) in record order: the
 // inputs of the neural constitutive model's network (coefficient pass)
-enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4, OP_NCM_INV = 5 };
+// OP_LINEARIZE writes each P1 element's linearisation at u (F^-T, w mu,
+// w (mu - lambda ln J), w lambda: 12 values, record order) for HVPs at the
+// same state (the PCG of a Newton step), which then skip u, F and its
+// inverse and logarithm (tile_kernel<..., LIN>)
+enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4, OP_NCM_INV = 5, OP_LINEARIZE = 6 };
+constexpr int kLinVals = 12;  // per element: F^-T (9), w mu, w (mu - lambda ln J), w lambda
 
 template <int ET>
 struct ElemT;
@@ -105,7 +110,9 @@ __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int align128(int x) { return (x + 127) & ~127; }
 
 // nlp: the largest padded tile node count
-__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nlp, int rec_bytes) {
+// lin: the HVP from a stored linearisation (no u buffer; each ring stage
+// also carries the rounds' 32 x kLinVals values)
+__host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int nlp, int rec_bytes, bool lin = false) {
     SmemLayout L;
     const int D = et == 0 ? 2 : 3;
     const int VW = D == 2 ? 2 : 4;
@@ -115,7 +122,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     const bool need_acc = (op == OP_RESIDUAL || op == OP_HVP || op == OP_BLOCKDIAG);
     int o = 0;
     L.off_u = o;
-    o = align16(o + nlp * vec);
+    if (!lin) o = align16(o + nlp * vec);
     L.off_v = o;
     if (need_v) o = align16(o + nlp * vec);
     L.off_x = o;
@@ -131,7 +138,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     o = align16(o + kWarps * 4 * 8 + 16);
     L.off_tab = o;
     o = align16(o + kMaxTilesPerCta * 16);
-    L.stage_bytes = rounds_per_iter(et, tsize, op) * rec_bytes;
+    L.stage_bytes = rounds_per_iter(et, tsize, op) * (rec_bytes + (lin ? 32 * kLinVals * tsize : 0));
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
     L.off_bar = o = align16(o);
@@ -178,6 +185,9 @@ struct KParams {
     // [2] per element (OP_NCM_INV)
     const void* ncm_coef;
     void* ncm_inv;
+    // linearisation [n_rounds * 32][kLinVals] in record order (OP_LINEARIZE
+    // writes it, the LIN HVP streams it through the record ring)
+    void* lin;
     // call
     const void* u;
     const void* v;
@@ -216,6 +226,23 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// two bulk copies completing one mbarrier phase
+__device__ __forceinline__ void bulk_load2(void* dst0, const void* src0, uint32_t b0, void* dst1, const void* src1,
+                                           uint32_t b1, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(b0 + b1)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst0)),
+        "l"(src0), "r"(b0), "r"(smem_u32(bar))
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst1)),
+        "l"(src1), "r"(b1), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -509,15 +536,72 @@ struct NcmElem {
     NcmCoef<D, V> d;
 };
 
-template <int OP, int D, int NM1, class V, bool NCM = false>
+template <int OP, int D, int NM1, class V, bool NCM = false, bool LIN = false>
 __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D], const V (&g)[NM1][D],
                                         V wdJ, V mu, V lam, int valid, V (&f)[NM1 + 1][6],
                                         ScalarAcc<typename VT<V>::S>& acc, bool scal, double (&gmu)[2],
                                         double (&glam)[2], int& inv, const NcmElem<D, V>* ncm = nullptr,
-                                        typename VT<V>::S* ninv = nullptr) {
+                                        typename VT<V>::S* ninv = nullptr, const typename VT<V>::S* lv = nullptr) {
     using S = typename VT<V>::S;
     constexpr int N = VT<V>::N;
     static_assert(!NCM || N == 1, "the neural constitutive model runs one element per lane");
+    static_assert(!LIN || (N == 1 && OP == OP_HVP), "the stored linearisation serves the scalar HVP");
+    if constexpr (LIN) {
+        // dP = w mu dF + w (mu - lambda ln J) F^-T dF^T F^-T + w lambda tr(F^-1 dF) F^-T
+        // from the stored F^-T and scaled moduli (zero for empty or inverted lanes)
+        V FiT[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) FiT[i][j] = lv[i * D + j];
+        const V wmu = lv[9], c1 = lv[10], wlam = lv[11];
+        V trA = FiT[0][0] * dF[0][0];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                if (i + j > 0) trA = vfma(FiT[i][j], dF[i][j], trA);
+        V M[D][D];  // dF^T F^-T
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                V t = dF[0][a] * FiT[0][j];
+#pragma unroll
+                for (int l = 1; l < D; ++l) t = vfma(dF[l][a], FiT[l][j], t);
+                M[a][j] = t;
+            }
+        const V c2 = wlam * trA;
+        V P[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                V B = FiT[i][0] * M[0][j];
+#pragma unroll
+                for (int a = 1; a < D; ++a) B = vfma(FiT[i][a], M[a][j], B);
+                P[i][j] = vfma(c2, FiT[i][j], vfma(c1, B, wmu * dF[i][j]));
+            }
+        if (scal) {  // dP : dF
+            V e = P[0][0] * dF[0][0];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j)
+                    if (i + j > 0) e = vfma(P[i][j], dF[i][j], e);
+            acc.add0(vsel(valid, e, S(0)));
+        }
+#pragma unroll
+        for (int a = 0; a < NM1; ++a)
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                V t = f[a][i];
+#pragma unroll
+                for (int j = 0; j < D; ++j) t = vfma(P[i][j], g[a][j], t);
+                f[a][i] = t;
+            }
+        return;
+    }
     Kin<D, V> k;
     kinematics<D, V>(H, k);
     if constexpr (OP == OP_NCM_INV) {
@@ -535,6 +619,31 @@ __device__ __forceinline__ void qp_work(const V (&H)[D][D], const V (&dF)[D][D],
     }
     const int good = valid & k.ok;
     wdJ = vsel(good, wdJ, S(0));  // inverted or empty halves contribute nothing
+    if constexpr (OP == OP_LINEARIZE) {
+        static_assert(N == 1, "scalar lanes");
+        // every lane writes (16-byte stores): empty and inverted lanes get
+        // zero moduli; 2D uses the first four of the nine F^-T slots
+        S o[kLinVals];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) o[q] = S(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) o[i * D + j] = (i == j) ? k.G[i][j] + S(1) : k.G[i][j];
+        o[9] = wdJ * mu;
+        o[10] = wdJ * (mu - lam * k.lnJ);
+        o[11] = wdJ * lam;
+        if constexpr (sizeof(S) == 4) {
+#pragma unroll
+            for (int q = 0; q < kLinVals / 4; ++q)
+                reinterpret_cast<float4*>(ninv)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kLinVals / 2; ++q)
+                reinterpret_cast<double2*>(ninv)[q] = make_double2(o[2 * q], o[2 * q + 1]);
+        }
+        return;
+    }
     // the network's coefficients scaled by w det J (zero for bad lanes)
     NcmCoef<D, V> nc{};
     if constexpr (NCM) {
@@ -672,11 +781,12 @@ struct Packer<2, ET, T> {
 };
 
 // element of a round pair / single: gather, compute, return contributions
-template <int ET, typename T, int OP, class V, bool NCM = false>
+template <int ET, typename T, int OP, class V, bool NCM = false, bool LIN = false>
 __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, const T* sU, const T* sV,
                                              const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc<T>& acc,
                                              bool scal, double (&gmu)[2], double (&glam)[2], int& inv,
-                                             const NcmElem<ElemT<ET>::D, V>* ncm = nullptr, T* ninv = nullptr) {
+                                             const NcmElem<ElemT<ET>::D, V>* ncm = nullptr, T* ninv = nullptr,
+                                             const T* lv = nullptr) {
     using E = ElemT<ET>;
     using S = typename VT<V>::S;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1, NG = E::NG;
@@ -687,14 +797,19 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
 #pragma unroll
     for (int a = 0; a < NEN; ++a) {
         T t0[4], t1[4];
-        lds_vec<VW, T>(sU, hs[0].cn[a], t0);
-        if constexpr (N == 2) lds_vec<VW, T>(sU, hs[N - 1].cn[a], t1);
+        if constexpr (LIN) {  // the stored linearisation replaces u
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            if constexpr (N == 2)
-                ue[a][c] = mk2(t0[c], t1[c]);
-            else
-                ue[a][c] = (V)t0[c];
+            for (int c = 0; c < D; ++c) ue[a][c] = splat<V>(S(0));
+        } else {
+            lds_vec<VW, T>(sU, hs[0].cn[a], t0);
+            if constexpr (N == 2) lds_vec<VW, T>(sU, hs[N - 1].cn[a], t1);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                if constexpr (N == 2)
+                    ue[a][c] = mk2(t0[c], t1[c]);
+                else
+                    ue[a][c] = (V)t0[c];
+            }
         }
         if constexpr (kNeedV) {
             lds_vec<VW, T>(sV, hs[0].cn[a], t0);
@@ -746,7 +861,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
         for (int a = 0; a <= NM1; ++a)
 #pragma unroll
             for (int c = 0; c < 6; ++c) fq[a][c] = splat<V>(S(0));
-        qp_work<OP, D, NM1, V, NCM>(H, dF, g, wdJ, mu, lam, valid, fq, acc, scal, gmu, glam, inv, ncm, ninv);
+        qp_work<OP, D, NM1, V, NCM, LIN>(H, dF, g, wdJ, mu, lam, valid, fq, acc, scal, gmu, glam, inv, ncm, ninv, lv);
         if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -766,7 +881,8 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
                 for (int c = 0; c < 6; ++c) f[a][c] = fq[a][c];
         }
     } else {
-        static_assert(!NCM && OP != OP_NCM_INV, "the neural constitutive model covers P1 elements");
+        static_assert(!NCM && !LIN && OP != OP_NCM_INV && OP != OP_LINEARIZE,
+                      "the neural constitutive model and the stored linearisation cover P1 elements");
         // Q1: reference node 0; J rebuilt at each Gauss point
         V dx[NM1][D], du[NM1][D], dv[NM1][D];
         {
@@ -965,13 +1081,17 @@ __device__ __forceinline__ void reduce_tiles(const double* tile_red, int n_tiles
 // ---------------------------------------------------------------------------
 constexpr int kEmptyLane = 0xFFFF;  // local id of an empty lane (the planner's kNoNode)
 
-// NCM: the neural constitutive model's terms from p.ncm_coef (P1 only)
-template <int ET, typename T, int OP, bool NCM = false>
-__global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
+// NCM: the neural constitutive model's terms from p.ncm_coef (P1 only).
+// LIN: the HVP from the linearisation p.lin stored by OP_LINEARIZE at the
+// same state (P1, Neo-Hookean; no u gather, no F, F^-1 or ln J)
+template <int ET, typename T, int OP, bool NCM, bool LIN>
+__device__ __forceinline__ void tile_body(const KParams& p) {
     using E = ElemT<ET>;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW;
     constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP);
-    constexpr bool kPacked = (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4 && !NCM && OP != OP_NCM_INV);
+    constexpr bool kPacked =
+        (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4 && !NCM && !LIN && OP != OP_NCM_INV && OP != OP_LINEARIZE);
+    static_assert(!LIN || (OP == OP_HVP && ET != 2 && !NCM), "the stored linearisation serves the P1 HVP");
     using V = typename std::conditional<kPacked, F2, T>::type;
     constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
@@ -981,7 +1101,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
     if (n_my == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes);
+    const SmemLayout L = smem_layout(ET, (int)sizeof(T), OP, p.max_nlp, p.rec_bytes, LIN);
     const int AW = L.aw;
     T* sAcc = reinterpret_cast<T*>(smem + L.off_acc);
     double* sRed = reinterpret_cast<double*>(smem + L.off_red);
@@ -1049,7 +1169,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             if (g < 0) return;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                cp_async<sizeof(T)>(bu + j * VW + c, gu + g * D + c);
+                if constexpr (!LIN) cp_async<sizeof(T)>(bu + j * VW + c, gu + g * D + c);
                 if constexpr (kNeedV) cp_async<sizeof(T)>(bv + j * VW + c, gv + g * D + c);
                 if constexpr (ET == 2) cp_async<sizeof(T)>(bx + j * VW + c, gx + g * D + c);
             }
@@ -1078,8 +1198,15 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             my_range(pi, p_r0, p_n);
         }
         const int nrec = min(NR, p_n - pit * NR);
-        bulk_load(ring + p_slot * L.stage_bytes, p.rec + (int64_t)(p_r0 + pit * NR) * p.rec_bytes,
-                  (uint32_t)(nrec * p.rec_bytes), &rbar[p_slot]);
+        const int64_t r0 = p_r0 + pit * NR;
+        if constexpr (LIN)  // the rounds' records, then their stored linearisation
+            bulk_load2(ring + p_slot * L.stage_bytes, p.rec + r0 * p.rec_bytes, (uint32_t)(nrec * p.rec_bytes),
+                       ring + p_slot * L.stage_bytes + NR * p.rec_bytes,
+                       static_cast<const unsigned char*>(p.lin) + r0 * 32 * kLinVals * (int64_t)sizeof(T),
+                       (uint32_t)(nrec * 32 * kLinVals * (int)sizeof(T)), &rbar[p_slot]);
+        else
+            bulk_load(ring + p_slot * L.stage_bytes, p.rec + r0 * p.rec_bytes, (uint32_t)(nrec * p.rec_bytes),
+                      &rbar[p_slot]);
         p_slot = (p_slot + 1 == kStages) ? 0 : p_slot + 1;
         ++pit;
         ++issued;
@@ -1119,7 +1246,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                fin = fin && finite_(sU[j * VW + c]);
+                if constexpr (!LIN) fin = fin && finite_(sU[j * VW + c]);
                 if constexpr (kNeedV) {
                     if (OP == OP_HVP && (p.flags & 2u) && ((m >> c) & 1)) sV[j * VW + c] = T(0);
                     fin = fin && finite_(sV[j * VW + c]);
@@ -1165,6 +1292,30 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
             for (int h = 0; h < NR; ++h) {
                 const bool ok = read_half<ET, T>(st + h * p.rec_bytes, lane, k0 + h < my_n, p, mu0, lam0, hs[h]);
                 valid |= ok ? (1 << h) : 0;
+            }
+            // the stored linearisation of this lane's elements, read before the
+            // stage is refilled (16-byte lane-major chunks: conflict-free)
+            T linv[LIN ? NR : 1][kLinVals];
+            if constexpr (LIN) {
+#pragma unroll
+                for (int h = 0; h < NR; ++h) {
+                    const bool here = k0 + h < my_n;
+                    const unsigned char* src = st + NR * p.rec_bytes + (size_t)(h * 32 + lane) * kLinVals * sizeof(T);
+                    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                        for (int q = 0; q < kLinVals / 4; ++q) {
+                            const float4 w = here ? reinterpret_cast<const float4*>(src)[q] : make_float4(0, 0, 0, 0);
+                            linv[h][4 * q] = w.x, linv[h][4 * q + 1] = w.y;
+                            linv[h][4 * q + 2] = w.z, linv[h][4 * q + 3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < kLinVals / 2; ++q) {
+                            const double2 w = here ? reinterpret_cast<const double2*>(src)[q] : make_double2(0, 0);
+                            linv[h][2 * q] = w.x, linv[h][2 * q + 1] = w.y;
+                        }
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) {
@@ -1238,8 +1389,12 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
                         }
                         T* ninv = nullptr;
                         if constexpr (OP == OP_NCM_INV) ninv = static_cast<T*>(p.ncm_inv) + rec * 2;
-                        element_work<ET, T, OP, V, NCM>(&hs[h], (valid >> h) & 1, sU, sV, sX, f[NF == 1 ? 0 : h],
-                                                        acc, want_scalar, gmu[h], glam[h], inv, &ne, ninv);
+                        if constexpr (OP == OP_LINEARIZE) ninv = static_cast<T*>(p.lin) + rec * kLinVals;
+                        const T* lv = nullptr;
+                        if constexpr (LIN) lv = linv[h];
+                        element_work<ET, T, OP, V, NCM, LIN>(&hs[h], (valid >> h) & 1, sU, sV, sX,
+                                                             f[NF == 1 ? 0 : h], acc, want_scalar, gmu[h], glam[h],
+                                                             inv, &ne, ninv, lv);
                     }
             }
             if constexpr (OP == OP_PVJP) {
@@ -1458,6 +1613,18 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     }
     __syncthreads();
     if (tid == 0 && *sFlag) atomicOr(p.status, *sFlag);
+}
+
+template <int ET, typename T, int OP, bool NCM = false, bool LIN = false>
+__global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
+    tile_body<ET, T, OP, NCM, LIN>(p);
+}
+
+// the FP32 HVP from a stored linearisation keeps to 102 registers, so that
+// five CTAs share an SM (its shared memory allows five)
+template <int ET>
+__global__ void __launch_bounds__(kThreads, 5) tile_kernel_lin(const KParams p) {
+    tile_body<ET, float, OP_HVP, false, true>(p);
 }
 
 // ---------------------------------------------------------------------------

@@ -860,6 +860,7 @@ private:
     SolverWork* w_;
     int D_, dt_, pi_;
     int64_t cg_max_;
+    bool lin_ = false;  // the PCG's HVPs read a stored linearisation
 
     int grid_nodes() const { return grid_for(w_->nn); }
     int grid_dofs() const { return grid_for(w_->nd); }
@@ -957,11 +958,12 @@ private:
         // w = K z with z . K z (fused), then the update
         // (both as programmatic dependent launches: each kernel's blocks are
         // placed while the previous kernel drains)
-        // (a neural constitutive model's coefficients at ucg are current: the
-        // preconditioner build evaluated them, and the state is fixed)
+        // the state is fixed: a neural constitutive model's coefficients at
+        // ucg are current (the preconditioner build evaluated them), and a
+        // Neo-Hookean P1 HVP reads the linearisation stored by pcg_t
+        const unsigned fixed_state = m_->ncm ? femi::kFlagNcmCurrent : (lin_ ? femi::kFlagUseLin : 0u);
         FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr,
-                             FEM_MASK_IN | FEM_MASK_OUT | femi::kFlagNcmCurrent, st_, &w->cg->done,
-                             /*vkv_tiles=*/1));
+                             FEM_MASK_IN | FEM_MASK_OUT | fixed_state, st_, &w->cg->done, /*vkv_tiles=*/1));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)cg_grid<D, T>());
         cfg.blockDim = dim3(kVT);
@@ -992,6 +994,10 @@ private:
         CUDA_TRY(cudaMemcpyAsync(&w->cg->tol2, &h->cg.tol2, sizeof(double), cudaMemcpyHostToDevice, st_));
         CUDA_TRY(cudaMemcpyAsync(&w->cg->cg_max, &h->cg.cg_max, sizeof(long long), cudaMemcpyHostToDevice, st_));
         using A = typename AccT<T>::type;
+        // the linearisation at ucg, read by every HVP of the solve
+        lin_ = !m_->ncm && m_->etype != FEM_HEX8;
+        if (lin_)
+            FEM_TRY(femi::run_op(m_, dt_, fem::OP_LINEARIZE, ucg, nullptr, nullptr, nullptr, 0, st_, nullptr));
         cg_init<D, T><<<cg_grid<D, T>(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],
                                                         (T*)w->z[pi], (T*)w->p[pi], (T*)w->s[pi],
                                                         (const T*)w->Minv[pi], w->cg, reinterpret_cast<A*>(w->partial));

@@ -23,6 +23,7 @@
 
 #include "fem_b300.h"
 #include "fem_internal.h"
+#include "fem_kernels.cuh"
 
 namespace femi {
 struct SparseData {
@@ -339,6 +340,10 @@ fem_status fem_sparse_assemble(fem_mesh* m, int dtype, const void* u, unsigned f
         S->seed[pi] = sd;
     }
     const int g = grid_for(S->n_dofs);
+    // one state for all colours: Neo-Hookean P1 meshes store the
+    // linearisation once and every seeded HVP reads it
+    const bool lin = !m->ncm && m->etype != FEM_HEX8;
+    if (lin) FEM_TRY(femi::run_op(m, dtype, fem::OP_LINEARIZE, u, nullptr, nullptr, nullptr, 0, st, nullptr));
     for (int32_t c = 0; c < S->n_colors; ++c) {
         void* col = static_cast<unsigned char*>(S->jcomp[pi]) + (size_t)c * S->n_dofs * es;
         if (dtype == FEM_F64)
@@ -346,7 +351,11 @@ fem_status fem_sparse_assemble(fem_mesh* m, int dtype, const void* u, unsigned f
         else
             seed_kernel<float><<<g, kT, 0, st>>>(S->n_dofs, S->d_colors, c, static_cast<float*>(S->seed[pi]));
         CUDA_TRY(cudaGetLastError());
-        FEM_TRY(fem_hvp(m, dtype, u, S->seed[pi], col, flags, nullptr, stream));
+        if (lin)
+            FEM_TRY(femi::run_op(m, dtype, fem::OP_HVP, u, S->seed[pi], col, nullptr, flags | femi::kFlagUseLin, st,
+                                 nullptr));
+        else
+            FEM_TRY(fem_hvp(m, dtype, u, S->seed[pi], col, flags, nullptr, stream));
     }
     const int gd = grid_for(S->n_dofs * 32);
     if (dtype == FEM_F64)
