@@ -49,6 +49,9 @@ namespace fem {
 #ifndef FEM_DUAL_ROUNDS
 #define FEM_DUAL_ROUNDS 1
 #endif
+#ifndef FEM_DUAL_LIN
+#define FEM_DUAL_LIN 0  // two rounds per iteration for the stored-linearisation HVP (measured slower)
+#endif
 constexpr int kWarps = FEM_TILE_WARPS;   // warps per tile (one accumulator copy each)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kStages = FEM_RING_STAGES;  // ring stages per warp
@@ -83,11 +86,13 @@ struct ElemT<2> {  // Q1 hexahedron, 2x2x2 Gauss
 // FP32x2 pairs; FEM_DUAL_ROUNDS gives each lane two independent elements (one
 // per round) computed with scalar arithmetic, so that their dependency chains
 // interleave, and fetches the two round records in one copy (FP32 P1 energy
-// and residual; the HVP's larger node buffers leave no room for the second
-// record in shared memory without losing a resident CTA)
-__host__ __device__ constexpr int rounds_per_iter(int et, int tsize, int op) {
+// and residual; with FEM_DUAL_LIN also the HVP from a stored linearisation,
+// which fits but measured slower; the full HVP's larger node buffers leave no
+// room for the second record in shared memory without losing a resident CTA)
+__host__ __device__ constexpr int rounds_per_iter(int et, int tsize, int op, bool lin = false) {
     return (et != 2 && tsize == 4 &&
-            (FEM_PAIR_FP32 || (FEM_DUAL_ROUNDS && (op == OP_ENERGY || op == OP_RESIDUAL))))
+            (FEM_PAIR_FP32 || (FEM_DUAL_ROUNDS && (op == OP_ENERGY || op == OP_RESIDUAL)) ||
+             (FEM_DUAL_LIN && lin && op == OP_HVP)))
                ? 2
                : 1;
 }
@@ -138,7 +143,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     o = align16(o + kWarps * 4 * 8 + 16);
     L.off_tab = o;
     o = align16(o + kMaxTilesPerCta * 16);
-    L.stage_bytes = rounds_per_iter(et, tsize, op) * (rec_bytes + (lin ? 32 * kLinVals * tsize : 0));
+    L.stage_bytes = rounds_per_iter(et, tsize, op, lin) * (rec_bytes + (lin ? 32 * kLinVals * tsize : 0));
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
     L.off_bar = o = align16(o);
@@ -1088,7 +1093,7 @@ template <int ET, typename T, int OP, bool NCM, bool LIN>
 __device__ __forceinline__ void tile_body(const KParams& p) {
     using E = ElemT<ET>;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW;
-    constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP);
+    constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP, LIN);
     constexpr bool kPacked =
         (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4 && !NCM && !LIN && OP != OP_NCM_INV && OP != OP_LINEARIZE);
     static_assert(!LIN || (OP == OP_HVP && ET != 2 && !NCM), "the stored linearisation serves the P1 HVP");
@@ -1620,10 +1625,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const KParams p) {
     tile_body<ET, T, OP, NCM, LIN>(p);
 }
 
-// the FP32 HVP from a stored linearisation keeps to 102 registers, so that
-// five CTAs share an SM (its shared memory allows five)
+// the FP32 HVP from a stored linearisation: two rounds per iteration within
+// the registers of four CTAs per SM (one round: within those of five)
 template <int ET>
-__global__ void __launch_bounds__(kThreads, 5) tile_kernel_lin(const KParams p) {
+__global__ void __launch_bounds__(kThreads, FEM_DUAL_LIN ? 4 : 5) tile_kernel_lin(const KParams p) {
     tile_body<ET, float, OP_HVP, false, true>(p);
 }
 
