@@ -42,8 +42,8 @@ class Shard:
 
 def partition(mesh: mg.Mesh, world: int, axis: int | None = None) -> list[Shard]:
     """Slabs of equal element counts along `axis` (default: the last)."""
-    if world < 1:
-        raise ValueError("world must be >= 1")
+    if world < 1 or world > mesh.n_el:
+        raise ValueError("world must be between 1 and the number of elements")
     axis = mesh.dim - 1 if axis is None else axis
     cen = mesh.coords[mesh.conn].mean(axis=1)[:, axis]
     order = np.lexsort((np.arange(mesh.n_el), cen))  # ties by element id

@@ -93,3 +93,10 @@ def test_halo_sum_on_gloo_ranks(kind, world):
             key = int(n)
             vals = (ra[k * d:(k + 1) * d].tobytes(), ya[k * d:(k + 1) * d].tobytes())
             assert seen.setdefault(key, vals) == vals
+
+
+def test_partition_rejects_more_ranks_than_elements():
+    m = mg.workload_tet(1)
+    with pytest.raises(ValueError):
+        sh.partition(m, m.n_el + 1)
+    assert len(sh.partition(m, m.n_el)) == m.n_el
