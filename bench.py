@@ -376,11 +376,20 @@ def atomic_arm(gm, ut, vt, t_res_us, t_hvp_us, flush_l2):
     t_r = timed(lambda: gm.residual_atomic(ut, out=r))
     t_h = timed(lambda: gm.hvp_atomic(ut, vt, out=y))
     y2 = gm.hvp_atomic(ut, vt)
+    # K itself: element stiffness scattered with atomics against Algorithm 2
+    k1 = gm.sparse_assemble_atomic(ut)
+    t_k = timed(lambda: gm.sparse_assemble_atomic(ut, out=k1), 5)
+    k2 = gm.sparse_assemble_atomic(ut)
+    kc = gm.sparse_assemble(ut)
+    t_kc = timed(lambda: gm.sparse_assemble(ut, out=kc), 5)
     return {"what": "one thread per element in mesh order, nodal forces added with float atomicAdd "
                     "(same constitutive code); the tiled kernels add in a fixed order",
             "residual_us": t_r, "hvp_us": t_h, "tiled_residual_us": t_res_us, "tiled_hvp_us": t_hvp_us,
             "slowdown_residual": t_r / t_res_us, "slowdown_hvp": t_h / t_hvp_us,
-            "hvp_entries_differing_between_two_runs": int((y2 != y).sum()), "n_dofs": gm.n_dofs}
+            "hvp_entries_differing_between_two_runs": int((y2 != y).sum()), "n_dofs": gm.n_dofs,
+            "K_assembly_atomic_ms": t_k / 1e3, "K_assembly_algorithm2_ms": t_kc / 1e3,
+            "K_entries_differing_between_two_runs": int((k2 != k1).sum()), "K_nnz": k1.numel(),
+            "K_atomic_vs_algorithm2_rel": float(torch.linalg.norm(k1 - kc) / torch.linalg.norm(kc))}
 
 
 NCM_H = 32

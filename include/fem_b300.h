@@ -470,6 +470,13 @@ fem_status fem_residual_atomic(fem_mesh* mesh, int dtype, const void* u, void* r
                                void* stream);
 fem_status fem_hvp_atomic(fem_mesh* mesh, int dtype, const void* u, const void* v, void* y, unsigned flags,
                           void* stream);
+/* The same ablation for the assembled K (the paper's "traditional scatter-add
+ * assembly"): each element's stiffness, column by column from the same
+ * tangent, added with atomicAdd into the CSR values of fem_sparse_pattern
+ * (zeroed first).  Arguments and flags as fem_sparse_assemble; the values
+ * agree with it to rounding, but not bit for bit from run to run. */
+fem_status fem_sparse_assemble_atomic(fem_mesh* mesh, int dtype, const void* u, unsigned flags, void* values,
+                                      void* stream);
 
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */

@@ -117,6 +117,7 @@ def lib():
             "fem_residual_atomic": [P, i32, P, P, u32, P],
             "fem_mesh_set_ncm": [P, i32, P],
             "fem_hvp_atomic": [P, i32, P, P, P, u32, P],
+            "fem_sparse_assemble_atomic": [P, i32, P, u32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -139,5 +140,6 @@ EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_pla
             "fem_lp_get_params", "fem_lp_set_params",
             "fem_lp_features", "fem_lp_blocks", "fem_lp_gradient", "fem_lp_train_step",
             "fem_sparse_info", "fem_sparse_pattern", "fem_sparse_pattern_desc", "fem_sparse_assemble",
-            "fem_sparse_spmv", "fem_residual_atomic", "fem_hvp_atomic", "fem_mesh_set_ncm",
+            "fem_sparse_spmv", "fem_residual_atomic", "fem_hvp_atomic", "fem_sparse_assemble_atomic",
+            "fem_mesh_set_ncm",
             "fem_last_error"]

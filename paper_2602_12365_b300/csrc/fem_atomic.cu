@@ -173,6 +173,102 @@ __global__ void __launch_bounds__(kT) atomic_kernel(int64_t ne, const int32_t* _
     }
 }
 
+// Traditional assembly of K: the element stiffness column by column (the
+// tangent on dF = e_j g_b^T for each vertex b and component j), each entry
+// added with atomicAdd at its place in the CSR values.  Row (a, i) of the
+// pattern holds D columns per node of N(a) in ascending order, so the entry
+// (a i, b j) sits at row_ptr[a D + i] + D pos(b in N(a)) + j.
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) assemble_kernel(int64_t ne, const int32_t* __restrict__ conn,
+                                                      const T* __restrict__ geo, const T* __restrict__ mod,
+                                                      const uint8_t* __restrict__ node_mask, const T* __restrict__ u,
+                                                      const int64_t* __restrict__ row_ptr,
+                                                      const int64_t* __restrict__ node_ptr,
+                                                      const int32_t* __restrict__ node_idx, T* __restrict__ vals,
+                                                      unsigned flags, int* status) {
+    constexpr int NEN = D + 1, NG = D * D + 1;
+    for (int64_t e = blockIdx.x * (int64_t)kT + threadIdx.x; e < ne; e += (int64_t)gridDim.x * kT) {
+        int nd[NEN];
+        uint8_t mk[NEN];
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) {
+            nd[a] = conn[e * NEN + a];
+            mk[a] = node_mask[nd[a]];
+        }
+        T g[NEN][D];  // all vertices (the last: minus the sum of the others)
+#pragma unroll
+        for (int k = 0; k < D; ++k) g[D][k] = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                g[a][k] = geo[e * NG + a * D + k];
+                g[D][k] -= g[a][k];
+            }
+        const T wdJ = geo[e * NG + D * D];
+        const T mu = mod[e * 2] * wdJ, lam = mod[e * 2 + 1] * wdJ;
+        T H[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                T h = T(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) h = fma(u[(int64_t)nd[a] * D + i] - u[(int64_t)nd[D] * D + i], g[a][j], h);
+                H[i][j] = h;
+            }
+        fem::Kin<D, T> k;
+        fem::kinematics<D, T>(H, k);
+        if (!(k.ok & 1)) {
+            atomicOr(status, FEM_FLAG_INVERTED);
+            continue;
+        }
+        // where each vertex b sits in the node list of each vertex a
+        int64_t base[NEN][NEN];
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) {
+            const int64_t q0 = node_ptr[nd[a]], q1 = node_ptr[nd[a] + 1];
+            const int64_t r0 = row_ptr[(int64_t)nd[a] * D];
+#pragma unroll
+            for (int b = 0; b < NEN; ++b) {
+                int64_t lo = q0, hi = q1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (node_idx[mid] < nd[b])
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                base[a][b] = r0 + (lo - q0) * D;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NEN; ++b)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                if ((flags & FEM_MASK_IN) && ((mk[b] >> j) & 1)) continue;
+                T dF[D][D], dP[D][D];
+#pragma unroll
+                for (int r = 0; r < D; ++r)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) dF[r][c] = (r == j) ? g[b][c] : T(0);
+                fem::tangent<D, T>(dF, k, mu, lam, dP);
+#pragma unroll
+                for (int a = 0; a < NEN; ++a) {
+                    const int64_t rowlen = (node_ptr[nd[a] + 1] - node_ptr[nd[a]]) * D;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        if ((flags & FEM_MASK_OUT) && ((mk[a] >> i) & 1)) continue;
+                        T f = T(0);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) f = fma(dP[i][c], g[a][c], f);
+                        atomicAdd(vals + base[a][b] + i * rowlen + j, f);
+                    }
+                }
+            }
+    }
+}
+
 template <typename T>
 fem_status run(fem_mesh* m, int op, const void* u, const void* v, void* y, unsigned flags, cudaStream_t st) {
     const int pi = sizeof(T) == 8 ? 0 : 1;
@@ -205,6 +301,30 @@ fem_status run(fem_mesh* m, int op, const void* u, const void* v, void* y, unsig
     return FEM_OK;
 }
 
+template <typename T>
+fem_status run_assemble(fem_mesh* m, const void* u, void* vals, unsigned flags, cudaStream_t st) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    FEM_TRY(prepare<T>(m, pi));
+    const int64_t *row_ptr = nullptr, *node_ptr = nullptr;
+    const int32_t* node_idx = nullptr;
+    int64_t nnz = 0;
+    FEM_TRY(femi::sparse_arrays(m, &row_ptr, &node_ptr, &node_idx, &nnz));
+    const femi::AtomicData* A = m->atomic;
+    const int64_t ne = m->info.n_elems;
+    CUDA_TRY(cudaMemsetAsync(vals, 0, (size_t)nnz * sizeof(T), st));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ne + kT - 1) / kT, 148 * 16));
+    const T* gp = static_cast<const T*>(A->geo[pi]);
+    const T* mp = static_cast<const T*>(A->mod[pi]);
+    if (m->dim == 2)
+        assemble_kernel<2, T><<<grid, kT, 0, st>>>(ne, A->conn, gp, mp, m->node_mask, static_cast<const T*>(u), row_ptr,
+                                                   node_ptr, node_idx, static_cast<T*>(vals), flags, m->status);
+    else
+        assemble_kernel<3, T><<<grid, kT, 0, st>>>(ne, A->conn, gp, mp, m->node_mask, static_cast<const T*>(u), row_ptr,
+                                                   node_ptr, node_idx, static_cast<T*>(vals), flags, m->status);
+    CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
 fem_status dispatch(fem_mesh* m, int dtype, int op, const void* u, const void* v, void* y, unsigned flags,
                     void* stream) {
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
@@ -232,6 +352,20 @@ fem_status fem_hvp_atomic(fem_mesh* m, int dtype, const void* u, const void* v, 
     if (!u || !v || !y) return fail(FEM_ERR_ARG, "null u, v or y");
     if (y == u || y == v) return fail(FEM_ERR_ARG, "y must alias neither u nor v");
     return dispatch(m, dtype, fem::OP_HVP, u, v, y, flags, stream);
+}
+
+fem_status fem_sparse_assemble_atomic(fem_mesh* m, int dtype, const void* u, unsigned flags, void* values,
+                                      void* stream) {
+    if (!u || !values) return fail(FEM_ERR_ARG, "null u or values");
+    if (!m) return fail(FEM_ERR_ARG, "null mesh");
+    if (m->etype == FEM_HEX8) return fail(FEM_ERR_ARG, "the atomic-scatter ablation covers P1 elements only");
+    if (m->ncm) return fail(FEM_ERR_ARG, "the atomic-scatter ablation evaluates the Neo-Hookean law only");
+    if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
+    if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return dtype == FEM_F64 ? run_assemble<double>(m, u, values, flags, st)
+                            : run_assemble<float>(m, u, values, flags, st);
 }
 
 }  // extern "C"

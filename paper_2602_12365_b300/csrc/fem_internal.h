@@ -88,6 +88,10 @@ void lp_mesh_free(fem_mesh* m);
 void sparse_free(fem_mesh* m);
 // frees the atomic-ablation data of `m` (no-op without it)
 void atomic_free(fem_mesh* m);
+// the sparse pattern on the device (built on first use): CSR row pointers
+// over DOFs, and the node lists N(n) as a node CSR (fem_sparse.cu)
+fem_status sparse_arrays(fem_mesh* m, const int64_t** row_ptr, const int64_t** node_ptr, const int32_t** node_idx,
+                         int64_t* nnz);
 // neural constitutive model (fem_ncm.cu).  An internal flag of run_op /
 // launch: the network's coefficients are current for this u and dtype (a
 // PCG solve at a fixed state), so the coefficient pass is skipped.

@@ -286,6 +286,18 @@ int pix(int dtype) { return dtype == FEM_F64 ? 0 : 1; }
 
 }  // namespace
 
+namespace femi {
+fem_status sparse_arrays(fem_mesh* m, const int64_t** row_ptr, const int64_t** node_ptr, const int32_t** node_idx,
+                         int64_t* nnz) {
+    FEM_TRY(build_sparse(m));
+    *row_ptr = m->sparse->d_row_ptr;
+    *node_ptr = m->sparse->d_node_ptr;
+    *node_idx = m->sparse->d_node_idx;
+    *nnz = m->sparse->nnz;
+    return FEM_OK;
+}
+}  // namespace femi
+
 extern "C" {
 
 fem_status fem_sparse_info(fem_mesh* m, int64_t* nnz, int32_t* n_colors) {

@@ -221,6 +221,17 @@ class Mesh:
                                        _stream(stream)))
         return out
 
+    def sparse_assemble_atomic(self, u, mask_in=True, mask_out=True, out=None, stream=None):
+        """fem_sparse_assemble_atomic: K by element stiffness and atomic
+        scatter-add into the CSR values (run-to-run bit differences possible)."""
+        self._check_vec(u)
+        nnz, _ = self.sparse_info()
+        out = out if out is not None else torch.empty(nnz, dtype=u.dtype, device=u.device)
+        flags = (L.FEM_MASK_IN if mask_in else 0) | (L.FEM_MASK_OUT if mask_out else 0)
+        L.check(L.lib().fem_sparse_assemble_atomic(self._h, _dtype_code(u), _ptr(u), flags, _ptr(out),
+                                                   _stream(stream)))
+        return out
+
     # --- sparse K by colouring (Algorithm 2) ----------------------------------
     def sparse_info(self):
         """(nnz, n_colors) of K's DOF pattern and its distance-2 colouring

@@ -64,3 +64,15 @@ def test_ablation_rejects_hex_and_bad_dtype():
     g64 = Mesh.from_fixture(mt, precision="fp64")
     with pytest.raises(FemError):
         g64.residual_atomic(torch.zeros(mt.n_nodes * 3, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("precision,dt,tol", [("fp64", torch.float64, 1e-12), ("mixed", torch.float32, 1e-5)])
+@pytest.mark.parametrize("masked", [False, True])
+def test_atomic_assembly_matches_algorithm_2(precision, dt, tol, masked):
+    m = mg.workload_tet(5, seed=3, random_moduli=3)
+    gm = Mesh.from_fixture(m, precision=precision)
+    u = torch.as_tensor(mg.smooth_state(m, 0.5, amp=0.05).ravel(), dtype=dt, device="cuda")
+    ref = gm.sparse_assemble(u, mask_in=masked, mask_out=masked)
+    got = gm.sparse_assemble_atomic(u, mask_in=masked, mask_out=masked)
+    assert (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item() <= tol
+    assert gm.sync_status() == 0
