@@ -1280,7 +1280,7 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
         bool gathered = (i + 1 >= n_my);
         for (int it = 0; it < n_it && !timed_out; ++it) {
             const int s = c_slot;
-            if (!mbar_wait_bounded(&rbar[s], c_phase)) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&rbar[s], c_phase))) {  // warp-uniform
                 timed_out = true;
                 break;
             }
