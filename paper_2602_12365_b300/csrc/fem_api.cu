@@ -249,14 +249,20 @@ KFn pick_ncm(int op) {
 KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
     if (lin) {
         if (dtype == FEM_F64)
-            return et == 0 ? fem::tile_kernel<0, double, fem::OP_HVP, false, true>
-                           : fem::tile_kernel<1, double, fem::OP_HVP, false, true>;
-        return et == 0 ? fem::tile_kernel_lin<0> : fem::tile_kernel_lin<1>;
+            return et == 0   ? fem::tile_kernel<0, double, fem::OP_HVP, false, true>
+                   : et == 1 ? fem::tile_kernel<1, double, fem::OP_HVP, false, true>
+                             : fem::tile_kernel<2, double, fem::OP_HVP, false, true>;
+        return et == 0 ? fem::tile_kernel_lin<0>
+                       : (et == 1 ? fem::tile_kernel_lin<1> : fem::tile_kernel<2, float, fem::OP_HVP, false, true>);
     }
     if (op == fem::OP_LINEARIZE) {
         if (dtype == FEM_F64)
-            return et == 0 ? fem::tile_kernel<0, double, fem::OP_LINEARIZE> : fem::tile_kernel<1, double, fem::OP_LINEARIZE>;
-        return et == 0 ? fem::tile_kernel<0, float, fem::OP_LINEARIZE> : fem::tile_kernel<1, float, fem::OP_LINEARIZE>;
+            return et == 0   ? fem::tile_kernel<0, double, fem::OP_LINEARIZE>
+                   : et == 1 ? fem::tile_kernel<1, double, fem::OP_LINEARIZE>
+                             : fem::tile_kernel<2, double, fem::OP_LINEARIZE>;
+        return et == 0   ? fem::tile_kernel<0, float, fem::OP_LINEARIZE>
+               : et == 1 ? fem::tile_kernel<1, float, fem::OP_LINEARIZE>
+                         : fem::tile_kernel<2, float, fem::OP_LINEARIZE>;
     }
     if (ncm || op == fem::OP_NCM_INV) {
         if (dtype == FEM_F64) return et == 0 ? pick_ncm<0, double>(op) : pick_ncm<1, double>(op);
@@ -300,9 +306,12 @@ int worst_smem(int et, int nlp, bool mixed, bool mat) {
         w = std::max(w, fem::smem_layout(et, 8, op, nlp, record_bytes(et, mat, 8)).total);
         if (mixed) w = std::max(w, fem::smem_layout(et, 4, op, nlp, record_bytes(et, mat, 4)).total);
     }
-    if (et != 2) {  // the HVP from a stored linearisation
-        w = std::max(w, fem::smem_layout(et, 8, fem::OP_HVP, nlp, record_bytes(et, mat, 8), true).total);
-        if (mixed) w = std::max(w, fem::smem_layout(et, 4, fem::OP_HVP, nlp, record_bytes(et, mat, 4), true).total);
+    // the HVP from a stored linearisation, and the pass that stores it
+    w = std::max(w, fem::smem_layout(et, 8, fem::OP_HVP, nlp, record_bytes(et, mat, 8), true).total);
+    w = std::max(w, fem::smem_layout(et, 8, fem::OP_LINEARIZE, nlp, record_bytes(et, mat, 8)).total);
+    if (mixed) {
+        w = std::max(w, fem::smem_layout(et, 4, fem::OP_HVP, nlp, record_bytes(et, mat, 4), true).total);
+        w = std::max(w, fem::smem_layout(et, 4, fem::OP_LINEARIZE, nlp, record_bytes(et, mat, 4)).total);
     }
     return w;
 }
@@ -382,14 +391,15 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     }
     flags &= ~femi::kFlagNcmCurrent;
     // the stored linearisation: written by OP_LINEARIZE, read by an HVP that
-    // asks for it (P1, Neo-Hookean)
-    const bool lin = op == fem::OP_HVP && (flags & femi::kFlagUseLin) && !ncm && m->etype != 2;
+    // asks for it (Neo-Hookean; per element for P1, per Gauss point for Q1)
+    const bool lin = op == fem::OP_HVP && (flags & femi::kFlagUseLin) && !ncm;
     flags &= ~femi::kFlagUseLin;
     if (op == fem::OP_LINEARIZE) {
-        if (m->etype == 2 || m->ncm) return fail(FEM_ERR_ARG, "the stored linearisation covers Neo-Hookean P1 meshes");
+        if (m->ncm) return fail(FEM_ERR_ARG, "the stored linearisation covers the Neo-Hookean law");
         if (!m->lin[pi]) {
             void* q = nullptr;
-            fem_status s = zalloc(m, &q, (size_t)m->plan.n_rounds() * 32 * fem::kLinVals * tsize, st);
+            const size_t per_elem = m->etype == 2 ? 8 * fem::kHexLinVals : fem::kLinVals;
+            fem_status s = zalloc(m, &q, (size_t)m->plan.n_rounds() * 32 * per_elem * tsize, st);
             if (s != FEM_OK) return s;
             m->lin[pi] = q;
         }

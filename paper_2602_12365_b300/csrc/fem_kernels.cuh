@@ -66,6 +66,19 @@ constexpr int kFinThreads = 256;
 // inverse and logarithm (tile_kernel<..., LIN>)
 enum Op { OP_ENERGY = 0, OP_RESIDUAL = 1, OP_HVP = 2, OP_BLOCKDIAG = 3, OP_PVJP = 4, OP_NCM_INV = 5, OP_LINEARIZE = 6 };
 constexpr int kLinVals = 12;  // per element: F^-T (9), w mu, w (mu - lambda ln J), w lambda
+// Q1: per Gauss point A = F^-T J^-T (9), C = J^-1 J^-T (6: 00 11 22 01 02 12),
+// det J mu, det J (mu - lambda ln J), det J lambda, 2 zeros (J = dx/dxi);
+// stored lane-major in 16-byte chunks: chunk c of point q of lane l in
+// round r at ((r * 8 + q) * NCH + c) * 32 + l, NCH = kHexLinVals * size / 16
+constexpr int kHexLinVals = 20;
+template <typename T>
+__host__ __device__ constexpr int hex_lin_chunks() {
+    return kHexLinVals * (int)sizeof(T) / 16;
+}
+// Gauss points of the Q1 linearisation in flight per lane (a per-warp
+// shared-memory ring of [stage][chunk][lane] 16-byte chunks, filled by
+// cp.async kHexLinStages - 1 points ahead of their use)
+__host__ __device__ constexpr int hex_lin_stages(int tsize) { return tsize == 4 ? 3 : 2; }
 
 template <int ET>
 struct ElemT;
@@ -107,7 +120,7 @@ constexpr int kMaxTilesPerCta = 16;
 
 struct SmemLayout {
     int off_u, off_v, off_x, buf_bytes;  // inside one node buffer
-    int off_buf0, off_buf1, off_acc, acc_bytes, off_red, off_tab, off_ring, off_bar, total, aw,
+    int off_buf0, off_buf1, off_acc, acc_bytes, off_red, off_tab, off_ring, off_lin, off_bar, total, aw,
         stage_bytes;
 };
 
@@ -131,7 +144,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     L.off_v = o;
     if (need_v) o = align16(o + nlp * vec);
     L.off_x = o;
-    if (et == 2) o = align16(o + nlp * vec);
+    if (et == 2 && !lin) o = align16(o + nlp * vec);
     L.buf_bytes = align128(o);
     L.off_buf0 = 0;
     L.off_buf1 = L.buf_bytes;
@@ -143,9 +156,12 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     o = align16(o + kWarps * 4 * 8 + 16);
     L.off_tab = o;
     o = align16(o + kMaxTilesPerCta * 16);
-    L.stage_bytes = rounds_per_iter(et, tsize, op, lin) * (rec_bytes + (lin ? 32 * kLinVals * tsize : 0));
+    // (Q1 reads its per-point linearisation from global memory, not the ring)
+    L.stage_bytes = rounds_per_iter(et, tsize, op, lin) * (rec_bytes + (lin && et != 2 ? 32 * kLinVals * tsize : 0));
     L.off_ring = o = align128(o);
     o += kWarps * kStages * L.stage_bytes;
+    L.off_lin = o = align16(o);
+    if (et == 2 && lin) o += kWarps * hex_lin_stages(tsize) * 32 * kHexLinVals * tsize;
     L.off_bar = o = align16(o);
     o += kWarps * kStages * 8;
     L.total = align16(o);
@@ -293,6 +309,14 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// 16-byte global -> shared copy through L2 only
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void grid_dependency_wait() {
@@ -786,12 +810,138 @@ struct Packer<2, ET, T> {
 };
 
 // element of a round pair / single: gather, compute, return contributions
+// Q1 Gauss point of the stored linearisation.  With J = dx/dxi, physical
+// gradients J^-T dN/dxi and dF = dFr J^-1 (dFr = sum_a dv_a (x) dN_a/dxi),
+// the nodal forces det J dP J^-T dN_a/dxi need
+//   Q = det J dP J^-T = s1 dFr C + s2 A dFr^T A + s3 (A : dFr) A,
+// A = F^-T J^-T, C = J^-1 J^-T, s1 = det J mu, s2 = det J (mu - lambda ln J),
+// s3 = det J lambda (the tangent dP of the Neo-Hookean law, Sec. 2.1), and
+// Q : dFr = det J dP : dF.
+template <typename T>
+__device__ __forceinline__ void hex_linearize_point(const T (&H)[3][3], const T (&Ji)[3][3], T detJ, T mu, T lam,
+                                                    int valid, int& inv, ScalarAcc<T>& acc, T* dst) {
+    Kin<3, T> k;
+    kinematics<3, T>(H, k);
+    const int bad = valid & ~k.ok;
+    if (bad) {
+        inv |= bad;
+        acc.ninv += __popc(bad);
+    }
+    const bool good = (valid & k.ok) & 1;  // empty and inverted points store zeros
+    T o[kHexLinVals];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T a = T(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) a = fma(k.G[i][l] + (i == l ? T(1) : T(0)), Ji[j][l], a);
+            o[3 * i + j] = good ? a : T(0);
+        }
+    auto cij = [&](int i, int j) {
+        T c = Ji[i][0] * Ji[j][0];
+        c = fma(Ji[i][1], Ji[j][1], c);
+        c = fma(Ji[i][2], Ji[j][2], c);
+        return good ? c : T(0);
+    };
+    o[9] = cij(0, 0), o[10] = cij(1, 1), o[11] = cij(2, 2), o[12] = cij(0, 1), o[13] = cij(0, 2), o[14] = cij(1, 2);
+    o[15] = good ? detJ * mu : T(0);
+    o[16] = good ? detJ * (mu - lam * k.lnJ) : T(0);
+    o[17] = good ? detJ * lam : T(0);
+    o[18] = o[19] = T(0);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < kHexLinVals / 4; ++c)
+            reinterpret_cast<float4*>(dst)[c * 32] = make_float4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < kHexLinVals / 2; ++c)
+            reinterpret_cast<double2*>(dst)[c * 32] = make_double2(o[2 * c], o[2 * c + 1]);
+    }
+}
+
+// src: the lane's first chunk of the point in the shared-memory stage
+template <typename T>
+__device__ __forceinline__ void hex_lin_point(const T (&dv)[7][3], const T (&gr)[7][3], const T* src, int valid,
+                                              bool scal, ScalarAcc<T>& acc, T (&fr)[8][6]) {
+    T w[kHexLinVals];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < kHexLinVals / 4; ++c) {
+            const float4 t = reinterpret_cast<const float4*>(src)[c * 32];
+            w[4 * c] = t.x, w[4 * c + 1] = t.y, w[4 * c + 2] = t.z, w[4 * c + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < kHexLinVals / 2; ++c) {
+            const double2 t = reinterpret_cast<const double2*>(src)[c * 32];
+            w[2 * c] = t.x, w[2 * c + 1] = t.y;
+        }
+    }
+    T A[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[i][j] = w[3 * i + j];
+    const T C[3][3] = {{w[9], w[12], w[13]}, {w[12], w[10], w[14]}, {w[13], w[14], w[11]}};
+    const T s1 = w[15], s2 = w[16], s3 = w[17];
+    T dFr[3][3];
+    outer_sum<3, T>(dv, gr, 7, dFr);
+    T t = A[0][0] * dFr[0][0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (i + j > 0) t = fma(A[i][j], dFr[i][j], t);
+    T X[3][3];  // dFr^T A
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T x = dFr[0][a] * A[0][j];
+            x = fma(dFr[1][a], A[1][j], x);
+            X[a][j] = fma(dFr[2][a], A[2][j], x);
+        }
+    const T s3t = s3 * t;
+    T Q[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T m = dFr[i][0] * C[0][j];
+            m = fma(dFr[i][1], C[1][j], m);
+            m = fma(dFr[i][2], C[2][j], m);
+            T b = A[i][0] * X[0][j];
+            b = fma(A[i][1], X[1][j], b);
+            b = fma(A[i][2], X[2][j], b);
+            Q[i][j] = fma(s3t, A[i][j], fma(s2, b, s1 * m));
+        }
+    if (scal) {  // det J dP : dF
+        T e = Q[0][0] * dFr[0][0];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (i + j > 0) e = fma(Q[i][j], dFr[i][j], e);
+        acc.add0((valid & 1) ? e : T(0));
+    }
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T f = fr[a][i];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) f = fma(Q[i][j], gr[a][j], f);
+            fr[a][i] = f;
+        }
+}
+
 template <int ET, typename T, int OP, class V, bool NCM = false, bool LIN = false>
 __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, const T* sU, const T* sV,
                                              const T* sX, V (&f)[ElemT<ET>::NEN][6], ScalarAcc<T>& acc,
                                              bool scal, double (&gmu)[2], double (&glam)[2], int& inv,
                                              const NcmElem<ElemT<ET>::D, V>* ncm = nullptr, T* ninv = nullptr,
-                                             const T* lv = nullptr) {
+                                             const T* lv = nullptr, T* lbuf = nullptr) {
     using E = ElemT<ET>;
     using S = typename VT<V>::S;
     constexpr int D = E::D, NEN = E::NEN, VW = E::VW, NM1 = NEN - 1, NG = E::NG;
@@ -886,11 +1036,18 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
                 for (int c = 0; c < 6; ++c) f[a][c] = fq[a][c];
         }
     } else {
-        static_assert(!NCM && !LIN && OP != OP_NCM_INV && OP != OP_LINEARIZE,
-                      "the neural constitutive model and the stored linearisation cover P1 elements");
-        // Q1: reference node 0; J rebuilt at each Gauss point
+        static_assert(!NCM && OP != OP_NCM_INV, "the neural constitutive model covers P1 elements");
+        static_assert(!(LIN || OP == OP_LINEARIZE) || N == 1, "the stored linearisation runs one element per lane");
+        // Q1: reference node 0; J rebuilt at each Gauss point (or read with
+        // the point's stored linearisation)
+        constexpr int kChunk = 16 / (int)sizeof(T), kNch = hex_lin_chunks<T>();
         V dx[NM1][D], du[NM1][D], dv[NM1][D];
-        {
+        if constexpr (LIN) {
+#pragma unroll
+            for (int a = 1; a < NEN; ++a)
+#pragma unroll
+                for (int c = 0; c < D; ++c) dv[a - 1][c] = ve[a][c] - ve[0][c];
+        } else {
             T x0[4];
             lds_vec<VW, T>(sX, hs[0].cn[0], x0);
 #pragma unroll
@@ -910,6 +1067,24 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
         for (int a = 0; a < NEN; ++a)
 #pragma unroll
             for (int c = 0; c < 6; ++c) fr[a][c] = splat<V>(S(0));
+        // the stored linearisation: this lane's chunks of point q (global,
+        // lane-major) into stage q % kSt of the warp's ring by cp.async, one
+        // commit group per point (empty groups keep the count uniform)
+        constexpr int kSt = hex_lin_stages((int)sizeof(T));
+        const int lane_ = threadIdx.x & 31;
+        auto lin_issue = [&](int q) {
+            if (q < 8) {
+                T* dst = lbuf + ((q % kSt) * kNch * 32 + lane_) * kChunk;
+                const T* src = lv + q * kNch * 32 * kChunk;
+#pragma unroll
+                for (int c = 0; c < kNch; ++c) cp_async_cg16(dst + c * 32 * kChunk, src + c * 32 * kChunk);
+            }
+            cp_async_commit();
+        };
+        if constexpr (LIN) {
+#pragma unroll
+            for (int q = 0; q < kSt - 1; ++q) lin_issue(q);
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             V gr[NM1][D];
@@ -917,6 +1092,12 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
             for (int a = 0; a < NM1; ++a)
 #pragma unroll
                 for (int j = 0; j < D; ++j) gr[a][j] = (V)hex_dN(a + 1, q, j);
+            if constexpr (LIN) {
+                lin_issue(q + kSt - 1);
+                cp_async_wait_group<kSt - 1>();  // point q has landed
+                hex_lin_point<T>(dv, gr, lbuf + ((q % kSt) * kNch * 32 + lane_) * kChunk, valid, scal, acc, fr);
+                continue;
+            }
             V Jm[D][D];
             outer_sum<D, V>(dx, gr, NM1, Jm);
             const V c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
@@ -946,6 +1127,10 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
                 }
             V H[D][D], dF[D][D];
             outer_sum<D, V>(du, g, NM1, H);
+            if constexpr (OP == OP_LINEARIZE) {
+                hex_linearize_point<T>(H, Ji, detJ, mu, lam, valid, inv, acc, ninv + q * kNch * 32 * kChunk);
+                continue;
+            }
             if constexpr (kNeedV) {
                 outer_sum<D, V>(dv, g, NM1, dF);
             } else {
@@ -1096,7 +1281,7 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
     constexpr int NR = rounds_per_iter(ET, (int)sizeof(T), OP, LIN);
     constexpr bool kPacked =
         (FEM_PAIR_FP32 && ET != 2 && sizeof(T) == 4 && !NCM && !LIN && OP != OP_NCM_INV && OP != OP_LINEARIZE);
-    static_assert(!LIN || (OP == OP_HVP && ET != 2 && !NCM), "the stored linearisation serves the P1 HVP");
+    static_assert(!LIN || (OP == OP_HVP && !NCM), "the stored linearisation serves the Neo-Hookean HVP");
     using V = typename std::conditional<kPacked, F2, T>::type;
     constexpr bool kNeedV = (OP == OP_HVP || OP == OP_PVJP);
     constexpr bool kNeedAcc = (OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_BLOCKDIAG);
@@ -1176,7 +1361,7 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
             for (int c = 0; c < D; ++c) {
                 if constexpr (!LIN) cp_async<sizeof(T)>(bu + j * VW + c, gu + g * D + c);
                 if constexpr (kNeedV) cp_async<sizeof(T)>(bv + j * VW + c, gv + g * D + c);
-                if constexpr (ET == 2) cp_async<sizeof(T)>(bx + j * VW + c, gx + g * D + c);
+                if constexpr (ET == 2 && !LIN) cp_async<sizeof(T)>(bx + j * VW + c, gx + g * D + c);
             }
         };
 #pragma unroll
@@ -1204,7 +1389,7 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
         }
         const int nrec = min(NR, p_n - pit * NR);
         const int64_t r0 = p_r0 + pit * NR;
-        if constexpr (LIN)  // the rounds' records, then their stored linearisation
+        if constexpr (LIN && ET != 2)  // the rounds' records, then their stored linearisation
             bulk_load2(ring + p_slot * L.stage_bytes, p.rec + r0 * p.rec_bytes, (uint32_t)(nrec * p.rec_bytes),
                        ring + p_slot * L.stage_bytes + NR * p.rec_bytes,
                        static_cast<const unsigned char*>(p.lin) + r0 * 32 * kLinVals * (int64_t)sizeof(T),
@@ -1212,6 +1397,7 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
         else
             bulk_load(ring + p_slot * L.stage_bytes, p.rec + r0 * p.rec_bytes, (uint32_t)(nrec * p.rec_bytes),
                       &rbar[p_slot]);
+
         p_slot = (p_slot + 1 == kStages) ? 0 : p_slot + 1;
         ++pit;
         ++issued;
@@ -1300,8 +1486,8 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
             }
             // the stored linearisation of this lane's elements, read before the
             // stage is refilled (16-byte lane-major chunks: conflict-free)
-            T linv[LIN ? NR : 1][kLinVals];
-            if constexpr (LIN) {
+            T linv[LIN && ET != 2 ? NR : 1][kLinVals];
+            if constexpr (LIN && ET != 2) {
 #pragma unroll
                 for (int h = 0; h < NR; ++h) {
                     const bool here = k0 + h < my_n;
@@ -1394,12 +1580,18 @@ __device__ __forceinline__ void tile_body(const KParams& p) {
                         }
                         T* ninv = nullptr;
                         if constexpr (OP == OP_NCM_INV) ninv = static_cast<T*>(p.ncm_inv) + rec * 2;
-                        if constexpr (OP == OP_LINEARIZE) ninv = static_cast<T*>(p.lin) + rec * kLinVals;
+                        // Q1: the lane's first 16-byte chunk of the round (lane-major)
+                        const int64_t hex_lin = ((int64_t)(my_r0 + k0 + h) * 8 * hex_lin_chunks<T>() * 32 + lane) *
+                                                (16 / (int64_t)sizeof(T));
+                        if constexpr (OP == OP_LINEARIZE)
+                            ninv = static_cast<T*>(p.lin) + (ET == 2 ? hex_lin : rec * kLinVals);
                         const T* lv = nullptr;
-                        if constexpr (LIN) lv = linv[h];
+                        if constexpr (LIN) lv = ET == 2 ? static_cast<const T*>(p.lin) + hex_lin : linv[h];
+                        T* lbuf = reinterpret_cast<T*>(smem + L.off_lin) +
+                                  (size_t)warp * hex_lin_stages((int)sizeof(T)) * 32 * kHexLinVals;
                         element_work<ET, T, OP, V, NCM, LIN>(&hs[h], (valid >> h) & 1, sU, sV, sX,
                                                              f[NF == 1 ? 0 : h], acc, want_scalar, gmu[h], glam[h],
-                                                             inv, &ne, ninv, lv);
+                                                             inv, &ne, ninv, lv, lbuf);
                     }
             }
             if constexpr (OP == OP_PVJP) {

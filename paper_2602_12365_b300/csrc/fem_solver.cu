@@ -960,7 +960,7 @@ private:
         // placed while the previous kernel drains)
         // the state is fixed: a neural constitutive model's coefficients at
         // ucg are current (the preconditioner build evaluated them), and a
-        // Neo-Hookean P1 HVP reads the linearisation stored by pcg_t
+        // Neo-Hookean HVP reads the linearisation stored by pcg_t
         const unsigned fixed_state = m_->ncm ? femi::kFlagNcmCurrent : (lin_ ? femi::kFlagUseLin : 0u);
         FEM_TRY(femi::run_op(m_, dt_, fem::OP_HVP, ucg, w->z[pi], w->q[pi], nullptr,
                              FEM_MASK_IN | FEM_MASK_OUT | fixed_state, st_, &w->cg->done, /*vkv_tiles=*/1));
@@ -995,7 +995,7 @@ private:
         CUDA_TRY(cudaMemcpyAsync(&w->cg->cg_max, &h->cg.cg_max, sizeof(long long), cudaMemcpyHostToDevice, st_));
         using A = typename AccT<T>::type;
         // the linearisation at ucg, read by every HVP of the solve
-        lin_ = !m_->ncm && m_->etype != FEM_HEX8;
+        lin_ = !m_->ncm;
         if (lin_)
             FEM_TRY(femi::run_op(m_, dt_, fem::OP_LINEARIZE, ucg, nullptr, nullptr, nullptr, 0, st_, nullptr));
         cg_init<D, T><<<cg_grid<D, T>(), kVT, 0, st_>>>(w->nn, (const T*)w->b[pi], (T*)w->x[pi], (T*)w->res[pi],

@@ -352,9 +352,9 @@ fem_status fem_sparse_assemble(fem_mesh* m, int dtype, const void* u, unsigned f
         S->seed[pi] = sd;
     }
     const int g = grid_for(S->n_dofs);
-    // one state for all colours: Neo-Hookean P1 meshes store the
+    // one state for all colours: Neo-Hookean meshes store the
     // linearisation once and every seeded HVP reads it
-    const bool lin = !m->ncm && m->etype != FEM_HEX8;
+    const bool lin = !m->ncm;
     if (lin) FEM_TRY(femi::run_op(m, dtype, fem::OP_LINEARIZE, u, nullptr, nullptr, nullptr, 0, st, nullptr));
     for (int32_t c = 0; c < S->n_colors; ++c) {
         void* col = static_cast<unsigned char*>(S->jcomp[pi]) + (size_t)c * S->n_dofs * es;
