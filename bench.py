@@ -76,7 +76,7 @@ KERNEL_SOURCES = ("fem_api.cu", "fem_internal.h", "fem_kernels.cuh", "fem_materi
                   "fem_plan.h", "fem_vec.cuh")
 
 
-SPMV_SOURCES = ("fem_sparse.cu",)
+SPMV_SOURCES = ("fem_spmv.cu",)
 
 
 def kernel_source_hash(files=KERNEL_SOURCES):

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfem_b300.so")
-SOURCES = ["fem_plan.cpp", "fem_api.cu", "fem_solver.cu", "fem_learned.cu", "fem_sparse.cu", "fem_atomic.cu", "fem_ncm.cu"]
+SOURCES = ["fem_plan.cpp", "fem_api.cu", "fem_solver.cu", "fem_learned.cu", "fem_sparse.cu", "fem_spmv.cu", "fem_atomic.cu",
+           "fem_ncm.cu"]
 HEADERS = ["fem_plan.h", "fem_kernels.cuh", "fem_material.cuh", "fem_vec.cuh", "fem_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

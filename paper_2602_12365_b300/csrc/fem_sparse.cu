@@ -234,54 +234,6 @@ __global__ void __launch_bounds__(kT) decompress_kernel(int64_t n_rows, const in
     }
 }
 
-// y = K x on the CSR values, read through the pattern's block structure:
-// the D rows of node n hold the same columns, D per node p of N(n) in order,
-// so row (n, r) has value q D + b at column p D + b for the q-th node p of
-// N(n).  A half-warp takes node n; each lane sums a strided part of the
-// (q, b) entries for all D rows (one node id per entry instead of a column
-// index per value, and consecutive lanes on consecutive values), then a
-// fixed butterfly adds the parts.  (Measured on the 64^3 tet mesh: this
-// mapping beats a lane per D x D block and unrolled or register-capped
-// variants.)
-template <int D, typename T>
-__global__ void __launch_bounds__(kT) spmv_kernel(int64_t nn, const int64_t* __restrict__ row_ptr,
-                                                  const int64_t* __restrict__ node_ptr,
-                                                  const int32_t* __restrict__ node_idx, const T* __restrict__ vals,
-                                                  const T* __restrict__ x, T* __restrict__ y) {
-    constexpr int L = 16;
-    const int lane = threadIdx.x & 31, half = lane / L, sub = lane & (L - 1);
-    const int64_t warps = (int64_t)gridDim.x * (kT / 32);
-    // the loop bound is the same for all lanes of a warp (the shuffles need them all)
-    for (int64_t w = blockIdx.x * (int64_t)(kT / 32) + (threadIdx.x >> 5); 2 * w < nn; w += warps) {
-        const int64_t n = 2 * w + half;
-        T s[D];
-#pragma unroll
-        for (int r = 0; r < D; ++r) s[r] = T(0);
-        if (n < nn) {
-            const int64_t q0 = node_ptr[n];
-            const int len = (int)(node_ptr[n + 1] - q0) * D;  // entries per row
-            const T* v0 = vals + row_ptr[n * D];
-            for (int e = sub; e < len; e += L) {
-                const int q = e / D, b = e - q * D;
-                const T xv = x[(int64_t)node_idx[q0 + q] * D + b];
-#pragma unroll
-                for (int r = 0; r < D; ++r) s[r] += v0[(int64_t)r * len + e] * xv;
-            }
-        }
-#pragma unroll
-        for (int o = L / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int r = 0; r < D; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o, L);
-        if (n < nn && sub < D) {
-            T t = s[0];
-#pragma unroll
-            for (int r = 1; r < D; ++r)
-                if (sub == r) t = s[r];
-            y[n * D + sub] = t;
-        }
-    }
-}
-
 int pix(int dtype) { return dtype == FEM_F64 ? 0 : 1; }
 
 }  // namespace
@@ -382,37 +334,5 @@ fem_status fem_sparse_assemble(fem_mesh* m, int dtype, const void* u, unsigned f
     return FEM_OK;
 }
 
-fem_status fem_sparse_spmv(fem_mesh* m, int dtype, const void* values, const void* x, void* y, void* stream) {
-    if (!m) return fail(FEM_ERR_ARG, "null mesh");
-    if (!values || !x || !y) return fail(FEM_ERR_ARG, "null values, x or y");
-    if (x == y) return fail(FEM_ERR_ARG, "x and y must not alias");
-    if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
-    FEM_TRY(build_sparse(m));
-    const femi::SparseData* S = m->sparse;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t nn = m->info.n_nodes;
-    const int g = grid_for(nn * 16);
-    if (m->dim == 2) {
-        if (dtype == FEM_F64)
-            spmv_kernel<2, double><<<g, kT, 0, st>>>(nn, S->d_row_ptr, S->d_node_ptr, S->d_node_idx,
-                                                     static_cast<const double*>(values), static_cast<const double*>(x),
-                                                     static_cast<double*>(y));
-        else
-            spmv_kernel<2, float><<<g, kT, 0, st>>>(nn, S->d_row_ptr, S->d_node_ptr, S->d_node_idx,
-                                                    static_cast<const float*>(values), static_cast<const float*>(x),
-                                                    static_cast<float*>(y));
-    } else {
-        if (dtype == FEM_F64)
-            spmv_kernel<3, double><<<g, kT, 0, st>>>(nn, S->d_row_ptr, S->d_node_ptr, S->d_node_idx,
-                                                     static_cast<const double*>(values), static_cast<const double*>(x),
-                                                     static_cast<double*>(y));
-        else
-            spmv_kernel<3, float><<<g, kT, 0, st>>>(nn, S->d_row_ptr, S->d_node_ptr, S->d_node_idx,
-                                                    static_cast<const float*>(values), static_cast<const float*>(x),
-                                                    static_cast<float*>(y));
-    }
-    CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
-}
 
 }  // extern "C"
