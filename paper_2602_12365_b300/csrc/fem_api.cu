@@ -253,7 +253,7 @@ KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
                    : et == 1 ? fem::tile_kernel<1, double, fem::OP_HVP, false, true>
                              : fem::tile_kernel<2, double, fem::OP_HVP, false, true>;
         return et == 0 ? fem::tile_kernel_lin<0>
-                       : (et == 1 ? fem::tile_kernel_lin<1> : fem::tile_kernel<2, float, fem::OP_HVP, false, true>);
+                       : (et == 1 ? fem::tile_kernel_lin<1> : fem::tile_kernel_hex<fem::OP_HVP, true>);
     }
     if (op == fem::OP_LINEARIZE) {
         if (dtype == FEM_F64)
@@ -262,7 +262,7 @@ KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
                              : fem::tile_kernel<2, double, fem::OP_LINEARIZE>;
         return et == 0   ? fem::tile_kernel<0, float, fem::OP_LINEARIZE>
                : et == 1 ? fem::tile_kernel<1, float, fem::OP_LINEARIZE>
-                         : fem::tile_kernel<2, float, fem::OP_LINEARIZE>;
+                         : fem::tile_kernel_hex<fem::OP_LINEARIZE>;
     }
     if (ncm || op == fem::OP_NCM_INV) {
         if (dtype == FEM_F64) return et == 0 ? pick_ncm<0, double>(op) : pick_ncm<1, double>(op);
@@ -275,7 +275,13 @@ KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
     }
     if (et == 0) return pick<0, float>(op);
     if (et == 1) return pick<1, float>(op);
-    return pick<2, float>(op);
+    switch (op) {
+        case fem::OP_ENERGY: return fem::tile_kernel_hex<fem::OP_ENERGY>;
+        case fem::OP_RESIDUAL: return fem::tile_kernel_hex<fem::OP_RESIDUAL>;
+        case fem::OP_HVP: return fem::tile_kernel_hex<fem::OP_HVP>;
+        case fem::OP_BLOCKDIAG: return fem::tile_kernel_hex<fem::OP_BLOCKDIAG>;
+        default: return fem::tile_kernel_hex<fem::OP_PVJP>;
+    }
 }
 
 int max_optin_smem() {

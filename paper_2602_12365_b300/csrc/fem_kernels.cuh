@@ -1824,6 +1824,15 @@ __global__ void __launch_bounds__(kThreads, FEM_DUAL_LIN ? 4 : 5) tile_kernel_li
     tile_body<ET, float, OP_HVP, false, true>(p);
 }
 
+// FP32 Q1 operators with a register budget of FEM_HEX_MINB CTAs per SM
+#ifndef FEM_HEX_MINB
+#define FEM_HEX_MINB 2
+#endif
+template <int OP, bool LIN = false>
+__global__ void __launch_bounds__(kThreads, FEM_HEX_MINB) tile_kernel_hex(const KParams p) {
+    tile_body<2, float, OP, false, LIN>(p);
+}
+
 // ---------------------------------------------------------------------------
 // finalize: each shared node's partial slots summed in slot order, and nodes
 // of no element
