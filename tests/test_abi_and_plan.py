@@ -96,3 +96,23 @@ def test_plan_is_deterministic(lib):
     b = plan_partition(m.elem_type, m.coords, m.conn, 128)
     for x, y in zip(a[:4], b[:4]):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("n,tile", [(16, 512), (16, 256), (8, 256)])
+def test_structured_hex_rounds_are_full(lib, n, tile):
+    """On a structured Q1 grid whose tiles are boxes of at least 256 cells
+    (each cell parity then has a multiple of 32 cells), the class-first
+    colouring finds the 8 parities: every round holds 32 elements.  (Smaller
+    boxes cap a round at the parity class: 8 cells in a 4 x 4 x 4 box.)"""
+    from paper_2602_12365_b300.fem import plan_partition
+    m = mg.hex_mesh(n)
+    *_, info = plan_partition(m.elem_type, m.coords, m.conn, tile)
+    assert info["n_rounds"] == m.n_el // 32 and info["round_fill"] == 1.0
+
+
+def test_tet_round_fill_benchmark_family(lib):
+    """Kuhn tets (jittered): the rounds of 1024-element tiles stay nearly full."""
+    from paper_2602_12365_b300.fem import plan_partition
+    m = mg.tet_mesh(16, jitter_seed=1)
+    *_, info = plan_partition(m.elem_type, m.coords, m.conn, 0)
+    assert info["round_fill"] >= 0.97 and info["max_rounds"] <= 34
