@@ -391,11 +391,11 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
         if (s == FEM_OK)
             s = launch(m, dtype, fem::OP_NCM_INV, u, nullptr, nullptr, nullptr, nullptr, nullptr, 0, st, nullptr, skip,
                        0);
-        const int mode = op == fem::OP_ENERGY ? 0 : (op == fem::OP_RESIDUAL ? 1 : 2);
+        const int mode = op == fem::OP_ENERGY ? ((flags & femi::kFlagNcmGrad) ? 1 : 0) : (op == fem::OP_RESIDUAL ? 1 : 2);
         if (s == FEM_OK) s = femi::ncm_coefficients(m, dtype, mode, st, skip);
         if (s != FEM_OK) return s;
     }
-    flags &= ~femi::kFlagNcmCurrent;
+    flags &= ~(femi::kFlagNcmCurrent | femi::kFlagNcmGrad);
     // the stored linearisation: written by OP_LINEARIZE, read by an HVP that
     // asks for it (Neo-Hookean; per element for P1, per Gauss point for Q1)
     const bool lin = op == fem::OP_HVP && (flags & femi::kFlagUseLin) && !ncm;

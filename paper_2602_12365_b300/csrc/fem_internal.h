@@ -99,6 +99,11 @@ constexpr unsigned kFlagNcmCurrent = 1u << 16;
 // internal flag: an HVP at the state of the last OP_LINEARIZE call in this
 // precision (Neo-Hookean P1 meshes): it reads the stored linearisation
 constexpr unsigned kFlagUseLin = 1u << 17;
+// internal: an energy call prepares the network's coefficients with their
+// gradients too, so that a residual at the same state may follow with
+// kFlagNcmCurrent (the Newton line search: energy at the trial point, then,
+// once it is accepted, the residual there)
+constexpr unsigned kFlagNcmGrad = 1u << 18;
 void ncm_free(fem_mesh* m);
 // allocates the per-element arrays of `dtype` on first use
 fem_status ncm_prepare(fem_mesh* m, int dtype, cudaStream_t st);

@@ -889,9 +889,13 @@ private:
         return FEM_OK;
     }
 
-    // Psi(u) and the roundoff scale S (FP64)
+    // Psi(u) and the roundoff scale S (FP64).  With a neural constitutive
+    // model the call also leaves the network's gradient coefficients at u, so
+    // that residual(u, r, true) right after it skips the network (bitwise the
+    // same result: the same coefficients at the same state).
     fem_status energy(const double* u, double* psi, double* S) {
-        FEM_TRY(femi::run_op(m_, FEM_F64, fem::OP_ENERGY, u, nullptr, nullptr, w_->scal, 0, st_, nullptr));
+        FEM_TRY(femi::run_op(m_, FEM_F64, fem::OP_ENERGY, u, nullptr, nullptr, w_->scal,
+                             m_->ncm ? femi::kFlagNcmGrad : 0u, st_, nullptr));
         CUDA_TRY(cudaMemcpyAsync(w_->h->scal, w_->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st_));
         FEM_TRY(sync());
         *psi = w_->h->scal[0];
@@ -899,8 +903,11 @@ private:
         return FEM_OK;
     }
 
-    fem_status residual(const double* u, double* r) {
-        return femi::run_op(m_, FEM_F64, fem::OP_RESIDUAL, u, nullptr, r, nullptr, FEM_MASK_OUT, st_, nullptr);
+    // same_as_energy: u is the state of the last energy call, and no other
+    // FP64 call of the network has run since
+    fem_status residual(const double* u, double* r, bool same_as_energy = false) {
+        const unsigned keep = (same_as_energy && m_->ncm) ? femi::kFlagNcmCurrent : 0u;
+        return femi::run_op(m_, FEM_F64, fem::OP_RESIDUAL, u, nullptr, r, nullptr, FEM_MASK_OUT | keep, st_, nullptr);
     }
 
     // the state the CG's element kernels see: u itself (FP64) or its FP32 shadow
@@ -1088,7 +1095,7 @@ private:
         double psi = 0.0, S = 0.0;
         STEP_TRY(energy(u, &psi, &S));
         if (!std::isfinite(psi)) return 3;
-        STEP_TRY(residual(u, w->r));
+        STEP_TRY(residual(u, w->r, true));
         double rsq = 0.0;
         STEP_TRY(dot(w->r, FEM_F64, w->r, FEM_F64, &rsq));
         double rn = std::sqrt(rsq);
@@ -1124,7 +1131,7 @@ private:
                     if (pt <= psi + o_.armijo_c * alpha * g) {
                         ok = true;
                     } else if (std::fabs(pt - psi) <= 16.0 * kEps * S) {
-                        STEP_TRY(residual(w->ut, w->t));
+                        STEP_TRY(residual(w->ut, w->t, true));
                         double rtsq = 0.0;
                         STEP_TRY(dot(w->t, FEM_F64, w->t, FEM_F64, &rtsq));
                         if (std::sqrt(rtsq) < rn) ok = true;
@@ -1143,7 +1150,8 @@ private:
                 *err = fail(FEM_ERR_CUDA, "cudaMemcpyAsync (accept) failed");
                 return -1;
             }
-            STEP_TRY(residual(u, w->r));
+            // u is the accepted trial state, the last one the energy saw
+            STEP_TRY(residual(u, w->r, true));
             STEP_TRY(dot(w->r, FEM_F64, w->r, FEM_F64, &rsq));
             rn = std::sqrt(rsq);
         }
