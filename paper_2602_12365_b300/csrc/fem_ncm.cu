@@ -95,6 +95,29 @@ __device__ __forceinline__ float softplus_(float t) { return t > 20.f ? t : __lo
 __device__ __forceinline__ double softplus_(double t) { return t > 30.0 ? t : log1p(exp(t)); }
 __device__ __forceinline__ float sigmoid_(float t) { return __fdividef(1.f, 1.f + __expf(-t)); }
 __device__ __forceinline__ double sigmoid_(double t) { return 1.0 / (1.0 + exp(-t)); }
+// softplus and its derivative (the sigmoid) from one exponential: with
+// e = exp(t), softplus = log1p(e) and sigmoid = e / (1 + e); above the
+// softplus cut-off, softplus = t and the sigmoid keeps its own form
+__device__ __forceinline__ void softplus_sigmoid_(float t, float& sp, float& sg) {
+    if (t > 20.f) {
+        sp = t;
+        sg = sigmoid_(t);
+    } else {
+        const float e = __expf(t);
+        sp = __logf(1.f + e);
+        sg = __fdividef(e, 1.f + e);
+    }
+}
+__device__ __forceinline__ void softplus_sigmoid_(double t, double& sp, double& sg) {
+    if (t > 30.0) {
+        sp = t;
+        sg = sigmoid_(t);
+    } else {
+        const double e = exp(t);
+        sp = log1p(e);
+        sg = e / (1.0 + e);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void store8(T* dst, const T (&c)[8]) {
@@ -131,8 +154,10 @@ __global__ void __launch_bounds__(kT) ncm_coef_kernel(int64_t n, const T* __rest
 #pragma unroll
         for (int k = 0; k < H; ++k) {
             const T z = W1[2 * k] * I1 + W1[2 * k + 1] * J + b1[k];
-            a1[k] = softplus_(z);
-            if constexpr (MODE >= 1) s1[k] = sigmoid_(z);
+            if constexpr (MODE >= 1)
+                softplus_sigmoid_(z, a1[k], s1[k]);
+            else
+                a1[k] = softplus_(z);
             back[k] = T(0);
         }
         T y = w3[H], h00 = T(0), h01 = T(0), h11 = T(0);
@@ -141,9 +166,13 @@ __global__ void __launch_bounds__(kT) ncm_coef_kernel(int64_t n, const T* __rest
             T z2 = b2[m];
 #pragma unroll
             for (int k = 0; k < H; ++k) z2 += W2[m * H + k] * a1[k];
-            y += w3[m] * softplus_(z2);
+            T sp2, s2 = T(0);
+            if constexpr (MODE >= 1)
+                softplus_sigmoid_(z2, sp2, s2);
+            else
+                sp2 = softplus_(z2);
+            y += w3[m] * sp2;
             if constexpr (MODE >= 1) {
-                const T s2 = sigmoid_(z2);
                 const T gm = w3[m] * s2;
 #pragma unroll
                 for (int k = 0; k < H; ++k) back[k] += W2[m * H + k] * gm;
