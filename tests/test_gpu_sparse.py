@@ -142,3 +142,20 @@ def test_spmv_matches_host_csr(kind, dt):
         y = gm.sparse_spmv(vals, xt).double().cpu().numpy()
         assert np.all(np.abs(y - ref) <= tol * scale)
     assert gm.sync_status() == 0
+
+
+@pytest.mark.parametrize("kind,n,tile", [("hex", 1, 0), ("hex", 4, 16), ("tet", 1, 0), ("tet", 3, 40)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_assemble_edge_plans_match_oracle(kind, n, tile, precision, tol):
+    """Algorithm 2 through the stored linearisation on plans with a single
+    element (one lane of one round) and with many small tiles (partial
+    rounds, most nodes shared between tiles)."""
+    m = {"hex": lambda: mg.workload_hex(n, seed=4), "tet": lambda: mg.workload_tet(n, seed=4, random_moduli=4)}[kind]()
+    gm = Mesh.from_fixture(m, precision=precision, tile_elems=tile)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.as_tensor(_state(m), dtype=dt, device="cuda")
+    vals = gm.sparse_assemble(u, mask_in=False, mask_out=False)
+    om = oracle.OracleMesh.from_mesh(m)
+    _, _, ref = om.sparse_K(u.double().cpu().numpy(), mask_in=False, mask_out=False)
+    assert _rel(vals.double().cpu().numpy(), ref) <= tol
+    assert gm.sync_status() == 0
