@@ -63,7 +63,8 @@ typedef enum { FEM_F64 = 0, FEM_F32 = 1 } fem_dtype;
  * FP32 geometry for the FEM_F32 kernels and FP64 geometry for FEM_F64 ones. */
 typedef enum { FEM_PREC_FP64 = 0, FEM_PREC_MIXED = 1 } fem_precision;
 
-/* Flags for fem_residual / fem_hvp */
+/* Flags of fem_residual, fem_hvp, fem_sparse_assemble and the atomic
+ * variants; any other bit is rejected with FEM_ERR_ARG */
 #define FEM_MASK_OUT 1u /* zero prescribed components of the result          */
 #define FEM_MASK_IN 2u  /* zero prescribed components of v before use (HVP)  */
 #define FEM_MASK_BOTH (FEM_MASK_IN | FEM_MASK_OUT)

@@ -813,6 +813,7 @@ fem_status fem_energy_static(fem_mesh* m, int dtype, const void* u, double* out_
 fem_status fem_residual(fem_mesh* m, int dtype, const void* u, void* r, unsigned flags, void* stream) {
     if (!u || !r) return fail(FEM_ERR_ARG, "null u or r");
     if (u == r) return fail(FEM_ERR_ARG, "u and r must not alias");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     return launch(m, dtype, fem::OP_RESIDUAL, u, nullptr, r, nullptr, nullptr, nullptr, flags,
                   static_cast<cudaStream_t>(stream));
 }
@@ -821,6 +822,7 @@ fem_status fem_hvp(fem_mesh* m, int dtype, const void* u, const void* v, void* y
                    double* vKv_dev, void* stream) {
     if (!u || !v || !y) return fail(FEM_ERR_ARG, "null u, v or y");
     if (y == u || y == v) return fail(FEM_ERR_ARG, "y must alias neither u nor v");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     return launch(m, dtype, fem::OP_HVP, u, v, y, vKv_dev, nullptr, nullptr, flags,
                   static_cast<cudaStream_t>(stream));
 }

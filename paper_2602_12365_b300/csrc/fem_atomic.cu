@@ -344,6 +344,7 @@ extern "C" {
 fem_status fem_residual_atomic(fem_mesh* m, int dtype, const void* u, void* r, unsigned flags, void* stream) {
     if (!u || !r) return fail(FEM_ERR_ARG, "null u or r");
     if (u == r) return fail(FEM_ERR_ARG, "u and r must not alias");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     return dispatch(m, dtype, fem::OP_RESIDUAL, u, nullptr, r, flags, stream);
 }
 
@@ -351,6 +352,7 @@ fem_status fem_hvp_atomic(fem_mesh* m, int dtype, const void* u, const void* v, 
                           void* stream) {
     if (!u || !v || !y) return fail(FEM_ERR_ARG, "null u, v or y");
     if (y == u || y == v) return fail(FEM_ERR_ARG, "y must alias neither u nor v");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     return dispatch(m, dtype, fem::OP_HVP, u, v, y, flags, stream);
 }
 
@@ -358,6 +360,7 @@ fem_status fem_sparse_assemble_atomic(fem_mesh* m, int dtype, const void* u, uns
                                       void* stream) {
     if (!u || !values) return fail(FEM_ERR_ARG, "null u or values");
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     if (m->etype == FEM_HEX8) return fail(FEM_ERR_ARG, "the atomic-scatter ablation covers P1 elements only");
     if (m->ncm) return fail(FEM_ERR_ARG, "the atomic-scatter ablation evaluates the Neo-Hookean law only");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");

@@ -38,7 +38,7 @@ struct SparseData {
     int64_t* d_node_ptr = nullptr;  // N(n) as a node CSR (the pattern's block structure)
     int32_t* d_node_idx = nullptr;
     void* jcomp[2] = {nullptr, nullptr};  // [n_colors][n_dofs] per dtype (FP64, FP32)
-    void* seed[2] = {nullptr, nullptr};   // [n_dofs]
+    void* seeds[2] = {nullptr, nullptr};  // [n_colors][n_dofs]: e_c, built once per dtype
     std::vector<void*> allocs;
 };
 
@@ -212,12 +212,15 @@ fem_status build_sparse(fem_mesh* m) {
     return FEM_OK;
 }
 
-// e_c: 1 on the DOFs of colour c
+// the seeds of all colours: e_c[j] = 1 on the DOFs j of colour c ([n_colors][n])
 template <typename T>
-__global__ void __launch_bounds__(kT) seed_kernel(int64_t n, const int32_t* __restrict__ colors, int32_t c,
+__global__ void __launch_bounds__(kT) seed_kernel(int64_t n, int32_t n_colors, const int32_t* __restrict__ colors,
                                                   T* __restrict__ e) {
-    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < n; j += (int64_t)gridDim.x * kT)
-        e[j] = colors[j] == c ? T(1) : T(0);
+    const int64_t total = n * n_colors;
+    for (int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x; k < total; k += (int64_t)gridDim.x * kT) {
+        const int64_t c = k / n, j = k - c * n;
+        e[k] = colors[j] == (int32_t)c ? T(1) : T(0);
+    }
 }
 
 // Algorithm 2's decompression: K_ij = Jcomp[colour(j)][i], a warp per row
@@ -291,35 +294,35 @@ fem_status fem_sparse_assemble(fem_mesh* m, int dtype, const void* u, unsigned f
     if (!m) return fail(FEM_ERR_ARG, "null mesh");
     if (!u || !values) return fail(FEM_ERR_ARG, "null u or values");
     if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
+    if (flags & ~(unsigned)FEM_MASK_BOTH) return fail(FEM_ERR_ARG, "flags: only FEM_MASK_IN and FEM_MASK_OUT");
     FEM_TRY(build_sparse(m));
     femi::SparseData* S = m->sparse;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int pi = pix(dtype);
     const size_t es = dtype == FEM_F64 ? sizeof(double) : sizeof(float);
-    if (!S->jcomp[pi]) {
+    if (!S->jcomp[pi]) {  // workspace and the seeds of all colours, once per dtype
         unsigned char *jc = nullptr, *sd = nullptr;
         FEM_TRY(dalloc(S, &jc, (size_t)S->n_colors * S->n_dofs * es));
-        FEM_TRY(dalloc(S, &sd, (size_t)S->n_dofs * es));
+        FEM_TRY(dalloc(S, &sd, (size_t)S->n_colors * S->n_dofs * es));
+        const int gs = grid_for(S->n_dofs * S->n_colors);
+        if (dtype == FEM_F64)
+            seed_kernel<double><<<gs, kT, 0, st>>>(S->n_dofs, S->n_colors, S->d_colors, reinterpret_cast<double*>(sd));
+        else
+            seed_kernel<float><<<gs, kT, 0, st>>>(S->n_dofs, S->n_colors, S->d_colors, reinterpret_cast<float*>(sd));
+        CUDA_TRY(cudaGetLastError());
         S->jcomp[pi] = jc;
-        S->seed[pi] = sd;
+        S->seeds[pi] = sd;
     }
-    const int g = grid_for(S->n_dofs);
-    // one state for all colours: Neo-Hookean meshes store the
-    // linearisation once and every seeded HVP reads it
+    // one state for all colours: Neo-Hookean meshes store the linearisation
+    // once and every seeded HVP reads it; with a neural constitutive model
+    // the first HVP evaluates the network at u and the others reuse it
     const bool lin = !m->ncm;
     if (lin) FEM_TRY(femi::run_op(m, dtype, fem::OP_LINEARIZE, u, nullptr, nullptr, nullptr, 0, st, nullptr));
     for (int32_t c = 0; c < S->n_colors; ++c) {
         void* col = static_cast<unsigned char*>(S->jcomp[pi]) + (size_t)c * S->n_dofs * es;
-        if (dtype == FEM_F64)
-            seed_kernel<double><<<g, kT, 0, st>>>(S->n_dofs, S->d_colors, c, static_cast<double*>(S->seed[pi]));
-        else
-            seed_kernel<float><<<g, kT, 0, st>>>(S->n_dofs, S->d_colors, c, static_cast<float*>(S->seed[pi]));
-        CUDA_TRY(cudaGetLastError());
-        if (lin)
-            FEM_TRY(femi::run_op(m, dtype, fem::OP_HVP, u, S->seed[pi], col, nullptr, flags | femi::kFlagUseLin, st,
-                                 nullptr));
-        else
-            FEM_TRY(fem_hvp(m, dtype, u, S->seed[pi], col, flags, nullptr, stream));
+        const void* seed = static_cast<const unsigned char*>(S->seeds[pi]) + (size_t)c * S->n_dofs * es;
+        const unsigned fixed = lin ? femi::kFlagUseLin : (c > 0 ? femi::kFlagNcmCurrent : 0u);
+        FEM_TRY(femi::run_op(m, dtype, fem::OP_HVP, u, seed, col, nullptr, flags | fixed, st, nullptr));
     }
     const int gd = grid_for(S->n_dofs * 32);
     if (dtype == FEM_F64)

@@ -296,3 +296,24 @@ def test_full_size_hex_128():
     gm = Mesh.from_fixture(m)
     assert gm.info()["n_elems"] == 2_097_152
     _sampled_check(m, gm, torch.float32, n_sample=200)
+
+
+def test_unknown_flag_bits_are_rejected():
+    """Only FEM_MASK_IN / FEM_MASK_OUT reach the kernels from the public calls."""
+    import ctypes as C
+    from paper_2602_12365_b300 import _lib as L
+    from paper_2602_12365_b300._lib import FemError
+    from paper_2602_12365_b300.fem import Mesh
+    m = mg.workload_tet(2)
+    gm = Mesh.from_fixture(m)
+    u = torch.zeros(m.n_nodes * 3, dtype=torch.float32, device="cuda")
+    v, y = torch.ones_like(u), torch.empty_like(u)
+    for bit in (1 << 2, 1 << 16, 1 << 17, 1 << 18):
+        with pytest.raises(FemError, match="flags"):
+            L.check(L.lib().fem_hvp(gm._h, L.FEM_F32, C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr()),
+                                    C.c_void_p(y.data_ptr()), C.c_uint32(3 | bit), None, None))
+        with pytest.raises(FemError, match="flags"):
+            L.check(L.lib().fem_residual(gm._h, L.FEM_F32, C.c_void_p(u.data_ptr()), C.c_void_p(y.data_ptr()),
+                                         C.c_uint32(1 | bit), None))
+    gm.hvp(u, v, out=y)  # the handle still works
+    assert gm.sync_status() == 0
