@@ -118,6 +118,17 @@ def test_bitwise_reproducible_mixed():
     assert sa == sb
 
 
+@pytest.mark.parametrize("precision,dt", [("fp64", torch.float64), ("mixed", torch.float32)])
+def test_hex_bitwise_reproducible(precision, dt):
+    """Q1 load step through the per-point stored linearisation: the same
+    bits on every run (fixed-order sums, no atomics)."""
+    m = mg.workload_hex(4, seed=2)
+    a, sa, _ = _gpu_path(m, (0.05,), dt, precision=precision)
+    b, sb, _ = _gpu_path(m, (0.05,), dt, precision=precision)
+    assert np.array_equal(a, b)
+    assert sa == sb
+
+
 def test_result_independent_of_cg_batch():
     m = mg.workload_tet(5, seed=4)
     a, sa, _ = _gpu_path(m, (0.05,), torch.float32, cg_batch=1)
