@@ -151,6 +151,21 @@ fem_status fem_plan_partition(const fem_mesh_desc* desc, int32_t* elem_tile,
                               fem_mesh_info* info);
 
 /*
+ * fem_mesh_set_moduli -- replace the per-element moduli of a mesh created
+ * with per-element arrays (desc.mu / desc.lambda non-NULL), as a design loop
+ * does between solves (the moduli are the design variables of the adjoint
+ * gradient).  The geometry, plan and every allocation are kept; the (mu,
+ * lambda) slots of the round records of each precision are rewritten.
+ *   mu, lambda  HOST double[n_elems], element order of the description;
+ *               mu > 0, both finite (else FEM_ERR_ARG, nothing changed).
+ * FEM_ERR_ARG for a mesh created with scalar moduli.  Synchronises `stream`.
+ * Derived data that depend on the moduli (the learned preconditioner's node
+ * statistics, the scatter-add ablation's element arrays) are rebuilt on
+ * their next use; calls already enqueued on other streams must be complete.
+ */
+fem_status fem_mesh_set_moduli(fem_mesh* mesh, const double* mu, const double* lambda, void* stream);
+
+/*
  * fem_energy -- Psi_h(u) (Eq. 2) with per-element densities in the call's
  * dtype and an FP64 Neumaier-compensated, deterministic (fixed-order) sum.
  *   out_dev  DEVICE double[4]: [0] Psi_h (+inf if some J <= 0), [1] the
@@ -170,19 +185,23 @@ fem_status fem_energy(fem_mesh* mesh, int dtype, const void* u, double* out_dev,
  * counter, then FEM_STATIC_MAX_TILES x 4 doubles: 512 KiB + 256 B), one copy
  * per device and process.
  *   - A mesh with more than FEM_STATIC_MAX_TILES tiles (fem_mesh_info.n_tiles)
- *     is rejected with FEM_ERR_ARG and a message naming both numbers; nothing
- *     is enqueued.  At the default tile sizes the limit is 16.7M P1 or 8.4M Q1
- *     elements.
+ *     is rejected with FEM_ERR_ARG and a message naming both numbers.  At the
+ *     default tile sizes the limit is 16.7M P1 or 8.4M Q1 elements.  Every
+ *     rejected call (tile limit, null or bad argument, FEM_F32 on a mesh
+ *     without FP32 records) returns before it touches the shared array:
+ *     nothing is enqueued.
  *   - Each call enqueues, on `stream`, a 4-byte memset that zeroes the counter,
  *     then the kernel; the partials need no clearing (each tile writes its own
  *     before the last CTA reads them).
  *   - Overlapping calls race: every handle on the device shares the one
  *     array, so two calls in flight at once (two streams, two threads, two
  *     handles) give wrong sums.  Order them on one stream or by events.
- *   - The first call on each device does one-time host-side setup (looks up
- *     the array's device address with cudaGetSymbolAddress, sets the kernel's
- *     shared-memory limit, queries its occupancy); make that first call
- *     outside any stream capture.
+ *   - The first call in each CUDA context does one-time host-side setup
+ *     (looks up the array's device address with cudaGetSymbolAddress, with
+ *     that context's device current, sets the kernel's shared-memory limit,
+ *     queries its occupancy); make that first call outside any stream
+ *     capture.  The address is cached per context, so after a device reset
+ *     the next call looks it up again.
  * Arguments, output and status bits as for fem_energy.
  */
 #define FEM_STATIC_MAX_TILES 16384
@@ -324,6 +343,35 @@ fem_status fem_newton_step(fem_mesh* mesh, double* u, const double* ubar, double
  */
 fem_status fem_tangent_solve(fem_mesh* mesh, int cg_dtype, const double* u, const double* b, double* x,
                              double rtol, int64_t cg_max, int64_t* iters, void* stream);
+
+/*
+ * fem_compliance_gradient -- the adjoint design gradient of the compliance
+ * with respect to per-element shear moduli, the whole computation in the
+ * library (the paper's design-sensitivity use of the residual's derivatives,
+ * Sec. 2.1 with the inverse-design examples of Sec. 6).  Under pure
+ * displacement loading the compliance is the work of the prescribed
+ * displacements, c = u_c^T r_c(u*), r = grad Psi_h at the converged state u*;
+ * with lambda_e = ratio * mu_e tied,
+ *     dc/dmu_e = a^T (dr_e/dmu_e + ratio dr_e/dlambda_e),
+ *     a = u_c on prescribed DOFs, -lam on free ones,  K_ff lam = K_fc u_c.
+ * Steps (on `stream`): u_c from u and the mask; the unmasked FP64 residual
+ * and c = u_c . r (FP64, fixed order); K_fc u_c as one HVP with u_c as the
+ * direction (free rows); the adjoint PCG of fem_tangent_solve in cg_dtype
+ * (FP64 dot products); a; the per-element pass of fem_param_vjp in
+ * vjp_dtype; g_mu + ratio g_lam.
+ *   u      DEVICE double[n_nodes * dim], the converged state (the checkpoint of
+ *          the last load step: the law is hyperelastic, so the gradient
+ *          depends on the final state only).
+ *   dmu    DEVICE double[n_elems] (out), element order of the mesh description.
+ *   c_dev  DEVICE double[1] (out): the compliance.
+ *   iters  HOST (may be NULL): adjoint PCG iterations.
+ * Uses the Newton-CG workspace (allocated on first use, as fem_newton_step,
+ * plus one per-element array).  Synchronises `stream` (the PCG's stop test).
+ * Returns FEM_OK, FEM_ERR_ARG, FEM_ERR_NOT_SPD, FEM_ERR_NEG_CURVATURE,
+ * FEM_ERR_NOT_CONVERGED or FEM_ERR_CUDA.
+ */
+fem_status fem_compliance_gradient(fem_mesh* mesh, const double* u, double ratio, double rtol, int cg_dtype,
+                                   int vjp_dtype, double* dmu, double* c_dev, int64_t* iters, void* stream);
 
 /* ------------------------------------------------------------------------
  * Learned block preconditioner (3D meshes created FEM_PREC_MIXED; the PCG of
@@ -478,6 +526,19 @@ fem_status fem_hvp_atomic(fem_mesh* mesh, int dtype, const void* u, const void* 
  * agree with it to rounding, but not bit for bit from run to run. */
 fem_status fem_sparse_assemble_atomic(fem_mesh* mesh, int dtype, const void* u, unsigned flags, void* values,
                                       void* stream);
+
+/*
+ * fem_fp32_fma_rate -- a measurement helper with no counterpart in the paper:
+ * enqueues a kernel of `blocks` blocks of 256 threads, each thread running 8
+ * independent FP32 FMA chains of `iters` steps, so that the caller can time
+ * the GPU's FP32 FMA throughput (the roofline denominator of the ALU-bound
+ * Q1 element kernels) with events on `stream`.
+ *   out_dev  DEVICE float[blocks * 256], written (one value per thread, so
+ *            that the chains are not removed); caller-owned.
+ *   flops    HOST (may be NULL): the kernel's FP32 flops, FMA counted as 2.
+ * FEM_ERR_ARG for non-positive sizes or a null out_dev.
+ */
+fem_status fem_fp32_fma_rate(int blocks, int iters, float* out_dev, double* flops, void* stream);
 
 /* Synchronise `stream`, return the handle's status word (FEM_FLAG_*) in
  * *flags and clear it. */

@@ -118,6 +118,9 @@ def lib():
             "fem_mesh_set_ncm": [P, i32, P],
             "fem_hvp_atomic": [P, i32, P, P, P, u32, P],
             "fem_sparse_assemble_atomic": [P, i32, P, u32, P, P],
+            "fem_compliance_gradient": [P, P, C.c_double, C.c_double, i32, i32, P, P, C.POINTER(C.c_int64), P],
+            "fem_fp32_fma_rate": [i32, i32, P, C.POINTER(C.c_double), P],
+            "fem_mesh_set_moduli": [P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -141,5 +144,5 @@ EXPORTED = ["fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_pla
             "fem_lp_features", "fem_lp_blocks", "fem_lp_gradient", "fem_lp_train_step",
             "fem_sparse_info", "fem_sparse_pattern", "fem_sparse_pattern_desc", "fem_sparse_assemble",
             "fem_sparse_spmv", "fem_residual_atomic", "fem_hvp_atomic", "fem_sparse_assemble_atomic",
-            "fem_mesh_set_ncm",
+            "fem_mesh_set_ncm", "fem_compliance_gradient", "fem_fp32_fma_rate", "fem_mesh_set_moduli",
             "fem_last_error"]

@@ -9,11 +9,12 @@ fixed:
 
 i.e. dc/dmu_e = a^T dr_e/dmu_e with a = (-lam on free DOFs, u_c on prescribed
 ones).  The moduli are tied as lambda_e = ratio * mu_e, so
-d/dmu_e = d/dmu_e + ratio d/dlambda_e, which fem_param_vjp returns per element
-as (g_mu, g_lam).  K_fc u_c is one masked HVP with u_c as the direction, and
-the adjoint solve is fem_tangent_solve (block-Jacobi PCG on the HVP kernel).
-The state u* is the checkpoint of the last converged load step: the material
-is hyperelastic, so the gradient depends on the final state only.
+d/dmu_e = d/dmu_e + ratio d/dlambda_e.  Every step (c, the right-hand side
+K_fc u_c as one HVP, the adjoint PCG, a, the per-element pass and the tied
+sum) runs in the library's fem_compliance_gradient; this module only
+marshals arguments.  The state u* is the checkpoint of the last converged load
+step: the material is hyperelastic, so the gradient depends on the final state
+only.
 """
 from __future__ import annotations
 
@@ -22,30 +23,10 @@ import torch
 from .fem import Mesh
 
 
-def compliance(mesh: Mesh, u: torch.Tensor, uc: torch.Tensor) -> float:
-    """c = u_c^T r(u) over the prescribed DOFs (uc is zero elsewhere), FP64."""
-    r = mesh.residual(u, mask_out=False)
-    return float(torch.dot(uc, r))
-
-
-def prescribed_part(mesh: Mesh, u: torch.Tensor) -> torch.Tensor:
-    """u on prescribed DOFs, 0 on free ones."""
-    return torch.where(mesh.dirichlet_mask(u.device), u, torch.zeros_like(u))
-
-
 def compliance_gradient(mesh: Mesh, u: torch.Tensor, ratio: float = 10.0, rtol: float = 1e-10,
                         cg_dtype=torch.float64, vjp_dtype=torch.float64):
     """Return (c, dc/dmu [n_elems] FP64, adjoint CG iterations) at the
     converged FP64 state u.  ``cg_dtype`` float32 runs the adjoint PCG in FP32
     with FP64 dot products; ``vjp_dtype`` is the element pass's arithmetic."""
-    uc = prescribed_part(mesh, u)
-    c = compliance(mesh, u, uc)
-    # K_fc u_c: the HVP with u_c as the direction, output masked to free DOFs
-    rhs = mesh.hvp(u, uc, mask_in=False, mask_out=True)
-    lam, iters = mesh.tangent_solve(u, rhs, rtol=rtol, cg_dtype=cg_dtype)
-    a = uc - lam  # lam vanishes on prescribed DOFs
-    if vjp_dtype == torch.float64:
-        g_mu, g_lam = mesh.param_vjp(u, a)
-    else:
-        g_mu, g_lam = mesh.param_vjp(u.to(vjp_dtype), a.to(vjp_dtype))
-    return c, g_mu + ratio * g_lam, iters
+    c, g, iters = mesh.compliance_gradient(u, ratio=ratio, rtol=rtol, cg_dtype=cg_dtype, vjp_dtype=vjp_dtype)
+    return float(c.item()), g, iters

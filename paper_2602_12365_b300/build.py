@@ -19,7 +19,7 @@ OBJ = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(HERE, "libfem_b300.so")
 SOURCES = ["fem_plan.cpp", "fem_api.cu", "fem_solver.cu", "fem_learned.cu", "fem_sparse.cu", "fem_spmv.cu", "fem_atomic.cu",
            "fem_ncm.cu", "fem_calib.cu"]
-HEADERS = ["fem_plan.h", "fem_kernels.cuh", "fem_material.cuh", "fem_vec.cuh", "fem_internal.h"]
+HEADERS = ["fem_plan.h", "fem_kernels.cuh", "fem_pair.cuh", "fem_material.cuh", "fem_vec.cuh", "fem_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -13,6 +13,13 @@
 #include "fem_b300.h"
 #include "fem_internal.h"
 #include "fem_kernels.cuh"
+#include "fem_pair.cuh"
+
+// the FP32 P1 residual and HVP through the pair kernels (0: the one-element
+// tile kernels)
+#ifndef FEM_PAIR_KERNELS
+#define FEM_PAIR_KERNELS 1
+#endif
 #include "fem_plan.h"
 
 static_assert(fem::kEmptyLane == fem::kNoNode, "kernel and planner agree on empty lanes");
@@ -221,6 +228,71 @@ void pack_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out
     }
 }
 
+// Pair records of the FP32 P1 pair kernels (fem_pair.cuh): for every tile,
+// warp by warp (warp w runs fem::pair_rounds(R, w) consecutive rounds of the
+// tile's R), the warp's rounds two at a time: A = its 2k-th round, B = the
+// next one or nothing.  Per lane: one 16-byte chunk of local node ids
+// (A's NEN, padded to 4, then B's; a lane without an element names the dummy
+// node `dummy`), the NG geometry values as (A, B) pairs in 16-byte chunks,
+// and (mu_A, mu_B, lam_A, lam_B) when the moduli vary per element.  Returns
+// the first pair of every tile in tile_pair_ptr.
+void pack_pair_records(fem_mesh* m, const fem_mesh_desc* d, std::vector<uint8_t>& out,
+                       std::vector<int32_t>& tile_pair_ptr, int dummy) {
+    const fem::Plan& P = m->plan;
+    const int D = m->dim;
+    const int NG = m->etype == 0 ? 5 : 10;
+    const int NCH = m->etype == 0 ? 3 : 5;
+    const int RB = fem::pair_rec_bytes(m->etype, m->per_elem_mat);
+    const int nt = P.n_tiles();
+    tile_pair_ptr.assign((size_t)nt + 1, 0);
+    for (int t = 0; t < nt; ++t) {
+        const int R = P.tile_round_ptr[t + 1] - P.tile_round_ptr[t];
+        tile_pair_ptr[t + 1] = tile_pair_ptr[t] + fem::pair_first(R, fem::kWarps);
+    }
+    out.assign((size_t)tile_pair_ptr[nt] * RB, 0);
+    m->pair_elem.assign((size_t)tile_pair_ptr[nt] * 64, -1);
+    double Xe[4 * 3], geo[10];
+    for (int t = 0; t < nt; ++t) {
+        const int32_t* gid = P.node_gid.data() + P.tile_node_ptr[t];
+        const int R = P.tile_round_ptr[t + 1] - P.tile_round_ptr[t];
+        int pr = tile_pair_ptr[t];
+        int r = P.tile_round_ptr[t];
+        for (int w = 0; w < fem::kWarps; ++w) {
+            const int nw = fem::pair_rounds(R, w);
+            for (int k = 0; k < nw; k += 2, ++pr) {
+                uint8_t* rec = out.data() + (size_t)pr * RB;
+                uint16_t* ids = reinterpret_cast<uint16_t*>(rec);
+                float* geo0 = reinterpret_cast<float*>(rec + 512);
+                float* mat = reinterpret_cast<float*>(rec + 512 * (1 + NCH));
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t rr = r + k + h;
+                    const bool have_round = k + h < nw;
+                    for (int l = 0; l < 32; ++l) {
+                        const bool valid = have_round && l < P.round_nvalid[rr];
+                        for (int a = 0; a < 4; ++a)
+                            ids[l * 8 + h * 4 + a] =
+                                (valid && a < m->n_en) ? P.round_conn[(rr * 32 + l) * P.n_en_pad + a] : (uint16_t)dummy;
+                        if (!valid) continue;  // zero geometry and moduli
+                        const int32_t e = P.round_elem[rr * 32 + l];
+                        m->pair_elem[(size_t)pr * 64 + l * 2 + h] = e;
+                        const uint16_t* c = P.round_conn.data() + (rr * 32 + l) * P.n_en_pad;
+                        for (int a = 0; a <= D; ++a)
+                            for (int q = 0; q < D; ++q) Xe[a * D + q] = d->coords[(size_t)gid[c[a]] * D + q];
+                        femi::p1_geometry(D, Xe, geo);
+                        // pair j of lane l: chunk j / 2, slot 2 (j % 2) + h
+                        for (int j = 0; j < NG; ++j) geo0[(j / 2) * 128 + l * 4 + 2 * (j % 2) + h] = (float)geo[j];
+                        if (m->per_elem_mat) {
+                            mat[l * 4 + h] = (float)d->mu[e];
+                            mat[l * 4 + 2 + h] = (float)d->lambda[e];
+                        }
+                    }
+                }
+            }
+            r += nw;
+        }
+    }
+}
+
 using KFn = void (*)(const fem::KParams);
 
 template <int ET, typename T>
@@ -244,6 +316,11 @@ KFn pick_ncm(int op) {
         case fem::OP_BLOCKDIAG: return fem::tile_kernel<ET, T, fem::OP_BLOCKDIAG, true>;
         default: return fem::tile_kernel<ET, T, fem::OP_NCM_INV>;
     }
+}
+
+KFn pair_kernel_for(int et, int op) {
+    if (op == fem::OP_HVP) return et == 0 ? fem::pair_kernel<0, fem::OP_HVP> : fem::pair_kernel<1, fem::OP_HVP>;
+    return et == 0 ? fem::pair_kernel<0, fem::OP_RESIDUAL> : fem::pair_kernel<1, fem::OP_RESIDUAL>;
 }
 
 KFn kernel_for(int et, int dtype, int op, bool ncm, bool lin = false) {
@@ -348,25 +425,56 @@ struct ReductionScratch {
     unsigned* counter;
 };
 
-// Device address of g_static_scratch on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// Device address of g_static_scratch in the current context.  The address
+// is looked up (cudaGetSymbolAddress, with the context's device current) the
+// first time a context calls, and cached keyed by the context handle, not by
+// the device ordinal: after a device reset or a primary-context teardown the
+// module is loaded again, the array may move, and the new context gets a
+// fresh lookup instead of a stale pointer.
+using CtxGetCurrentFn = int (*)(void**);  // cuCtxGetCurrent (CUresult, CUcontext*)
+
+fem_status current_context(void** ctx) {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    *ctx = nullptr;
+    if (!fn) return fail(FEM_ERR_CUDA, "cuCtxGetCurrent is not available from the driver");
+    if (fn(ctx) != 0 || !*ctx) return fail(FEM_ERR_CUDA, "no current CUDA context for the static scratch");
+    return FEM_OK;
+}
+
 fem_status static_scratch(ReductionScratch* out) {
-    constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static void* addr[kMaxDevices] = {};
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(FEM_ERR_ARG, "device ordinal out of range for static scratch");
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* a = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
-        if (e != cudaSuccess || !a)
+    static std::vector<std::pair<void*, void*>> addr;  // (context, device address)
+    auto lookup = [](void** a) -> fem_status {
+        const cudaError_t e = cudaGetSymbolAddress(a, g_static_scratch);
+        if (e != cudaSuccess || !*a)
             return fail(FEM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
                                           cudaGetErrorString(e));
-        addr[dev] = a;
+        return FEM_OK;
+    };
+    void* ctx = nullptr;
+    void* a = nullptr;
+    fem_status cs = current_context(&ctx);
+    if (cs != FEM_OK) {
+        // no context is current on this thread yet: the lookup makes the
+        // device's primary context current; then ask again
+        if ((cs = lookup(&a)) != FEM_OK || (cs = current_context(&ctx)) != FEM_OK) return cs;
     }
-    unsigned char* base = static_cast<unsigned char*>(addr[dev]);
+    std::lock_guard<std::mutex> lk(mu);
+    bool cached = false;
+    for (const auto& e : addr)
+        if (e.first == ctx) a = e.second, cached = true;
+    if (!cached) {
+        if (!a && (cs = lookup(&a)) != FEM_OK) return cs;
+        addr.emplace_back(ctx, a);
+    }
+    unsigned char* base = static_cast<unsigned char*>(a);
     out->counter = reinterpret_cast<unsigned*>(base);
     out->tile_red = reinterpret_cast<double*>(base + kStaticCounterBytes);
     return FEM_OK;
@@ -453,8 +561,17 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_mu = out_mu;
     p.out_lam = out_lam;
     p.flags = flags;
-    const int smem = fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi], lin).total;
-    KFn fn = kernel_for(m->etype, dtype, op, ncm, lin);
+    // FP32 P1 residual and HVP (Neo-Hookean, no vKv, own workspace): the pair
+    // kernels, two elements per lane in paired FP32 arithmetic
+    const bool pair = FEM_PAIR_KERNELS && dtype == FEM_F32 && m->prec != nullptr && !ncm && !lin &&
+                      scratch == nullptr &&
+                      (op == fem::OP_RESIDUAL || (op == fem::OP_HVP && out_scalar == nullptr && vkv_tiles == 0));
+    p.prec = m->prec;
+    p.prec_bytes = m->prec_bytes;
+    p.tile_pair_ptr = m->tile_pair_ptr;
+    const int smem = pair ? fem::pair_layout(m->etype, op, m->max_nlp, m->prec_bytes).total
+                          : fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi], lin).total;
+    KFn fn = pair ? pair_kernel_for(m->etype, op) : kernel_for(m->etype, dtype, op, ncm, lin);
     int grid = 0;
     {
         // raise the dynamic shared-memory limit once per (device, kernel)
@@ -741,6 +858,19 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
             }
         }
     }
+    if (mixed && m->etype < 2 && m->max_nlp < 0xFFFF) {
+        // pair records of the FP32 pair kernels (the dummy node is max_nlp)
+        std::vector<uint8_t> precs;
+        std::vector<int32_t> tpp;
+        pack_pair_records(m, d, precs, tpp, m->max_nlp);
+        m->prec_bytes = fem::pair_rec_bytes(m->etype, m->per_elem_mat);
+        if ((s = upload(m, &m->prec, precs.data(), precs.size(), st)) != FEM_OK) goto fail_out;
+        if ((s = upload(m, &m->tile_pair_ptr, tpp.data(), tpp.size(), st)) != FEM_OK) goto fail_out;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            s = fail(FEM_ERR_CUDA, "cudaStreamSynchronize failed during upload");
+            goto fail_out;
+        }
+    }
     {
         void* p = nullptr;
         const int aw = D == 2 ? 4 : 6;
@@ -780,6 +910,87 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     return FEM_OK;
 }
 
+fem_status fem_mesh_set_moduli(fem_mesh* m, const double* mu, const double* lambda, void* stream) {
+    if (!m || !mu || !lambda) return fail(FEM_ERR_ARG, "null mesh, mu or lambda");
+    if (!m->per_elem_mat)
+        return fail(FEM_ERR_ARG, "fem_mesh_set_moduli: the mesh was created with scalar moduli (no per-element slots)");
+    const int64_t ne = m->info.n_elems;
+    for (int64_t e = 0; e < ne; ++e)
+        if (!(mu[e] > 0.0) || !std::isfinite(mu[e]) || !std::isfinite(lambda[e]))
+            return fail(FEM_ERR_ARG, "fem_mesh_set_moduli: need finite mu > 0 and finite lambda");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const fem::Plan& P = m->plan;
+    const int NG = m->etype == 0 ? 5 : (m->etype == 1 ? 10 : 0);
+    const int64_t nr = P.n_rounds();
+    // the (mu, lambda) pairs of every round, in record order (empty lanes 0),
+    // copied into each round record's pair block by one strided copy per
+    // precision
+    for (int pi = 0; pi < 2; ++pi) {
+        if (!m->rec[pi]) continue;
+        const size_t ts = pi == 0 ? 8 : 4;
+        std::vector<uint8_t> pairs((size_t)nr * 32 * 2 * ts, 0);
+        for (int64_t r = 0; r < nr; ++r)
+            for (int l = 0; l < 32; ++l) {
+                const int32_t e = P.round_elem[r * 32 + l];
+                if (e < 0) continue;
+                uint8_t* dst = pairs.data() + ((size_t)r * 32 + l) * 2 * ts;
+                if (pi == 0) {
+                    const double v[2] = {mu[e], lambda[e]};
+                    std::memcpy(dst, v, sizeof v);
+                } else {
+                    const float v[2] = {(float)mu[e], (float)lambda[e]};
+                    std::memcpy(dst, v, sizeof v);
+                }
+            }
+        const size_t off = (size_t)m->conn_bytes + ts * 32 * NG;
+        CUDA_TRY(cudaMemcpy2DAsync(m->rec[pi] + off, (size_t)m->rec_bytes[pi], pairs.data(), 32 * 2 * ts, 32 * 2 * ts,
+                                   (size_t)nr, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));  // `pairs` is a host temporary
+    }
+    if (m->prec && m->per_elem_mat) {
+        // the (mu_A, mu_B, lam_A, lam_B) chunk of every pair record
+        const int NCH = m->etype == 0 ? 3 : 5;
+        const int64_t npr = (int64_t)(m->pair_elem.size() / 64);
+        std::vector<float> chunk((size_t)npr * 128, 0.f);
+        for (int64_t q = 0; q < npr; ++q)
+            for (int l = 0; l < 32; ++l)
+                for (int h = 0; h < 2; ++h) {
+                    const int32_t e = m->pair_elem[(size_t)q * 64 + l * 2 + h];
+                    if (e < 0) continue;
+                    chunk[(size_t)q * 128 + l * 4 + h] = (float)mu[e];
+                    chunk[(size_t)q * 128 + l * 4 + 2 + h] = (float)lambda[e];
+                }
+        CUDA_TRY(cudaMemcpy2DAsync(m->prec + 512 * (1 + NCH), (size_t)m->prec_bytes, chunk.data(), 512, 512,
+                                   (size_t)npr, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // host copies and what was derived from them: the ablation's element
+    // arrays and the learned preconditioner's per-node statistics are rebuilt
+    // on their next use
+    m->mu_host.assign(mu, mu + ne);
+    m->lam_host.assign(lambda, lambda + ne);
+    femi::atomic_free(m);
+    if (!m->conn_host.empty()) {
+        const int64_t nn = m->info.n_nodes;
+        std::vector<double> smu((size_t)nn, 0.0), slam((size_t)nn, 0.0), val((size_t)nn, 0.0);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int a = 0; a < m->n_en; ++a) {
+                const int32_t n = m->conn_host[e * m->n_en + a];
+                smu[n] += mu[e];
+                slam[n] += lambda[e];
+                val[n] += 1.0;
+            }
+        for (int64_t n = 0; n < nn; ++n) {
+            const double mb = val[n] > 0 ? smu[n] / val[n] : m->mu0;
+            const double lb = val[n] > 0 ? slam[n] / val[n] : m->lam0;
+            m->node_stats[n * 3 + 0] = (float)std::log(mb);
+            m->node_stats[n * 3 + 1] = (float)std::log(lb / mb);
+        }
+        femi::lp_mesh_free(m);
+    }
+    return FEM_OK;
+}
+
 fem_status fem_mesh_get_info(const fem_mesh* m, fem_mesh_info* info) {
     if (!m || !info) return fail(FEM_ERR_ARG, "null argument");
     *info = m->info;
@@ -800,6 +1011,12 @@ fem_status fem_energy_static(fem_mesh* m, int dtype, const void* u, double* out_
         return fail(FEM_ERR_ARG, "fem_energy_static: the mesh has " + std::to_string(n_tiles) +
                                      " tiles but the static scratch holds " + std::to_string(FEM_STATIC_MAX_TILES) +
                                      "; use fem_energy or larger tiles");
+    // every check of the call comes before the shared array is touched, so a
+    // rejected call enqueues nothing (not even the counter's memset, which
+    // would disturb another static call in flight)
+    if (dtype != FEM_F64 && dtype != FEM_F32) return fail(FEM_ERR_ARG, "dtype must be FEM_F64 or FEM_F32");
+    if (dtype == FEM_F32 && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");
     ReductionScratch scr{};
     fem_status s = static_scratch(&scr);
     if (s != FEM_OK) return s;

@@ -66,6 +66,13 @@ struct fem_mesh {
     femi::NcmData* ncm = nullptr;
     // stored linearisation per precision (OP_LINEARIZE; allocated on first use)
     void* lin[2] = {nullptr, nullptr};
+    // pair records of the FP32 P1 pair kernels (mixed-precision P1 meshes):
+    // records, first pair of every tile, and on the host the element of every
+    // (pair, lane, half) slot (-1 empty) for moduli updates
+    uint8_t* prec = nullptr;
+    int prec_bytes = 0;
+    int32_t* tile_pair_ptr = nullptr;
+    std::vector<int32_t> pair_elem;
 };
 
 namespace femi {

@@ -209,6 +209,11 @@ struct KParams {
     // linearisation [n_rounds * 32][kLinVals] in record order (OP_LINEARIZE
     // writes it, the LIN HVP streams it through the record ring)
     void* lin;
+    // pair records of the FP32 P1 pair kernels (fem_pair.cuh): two rounds
+    // per lane and record, tile by tile and warp by warp
+    const uint8_t* prec;
+    int prec_bytes;
+    const int32_t* tile_pair_ptr;
     // call
     const void* u;
     const void* v;

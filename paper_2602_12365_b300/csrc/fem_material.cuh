@@ -21,7 +21,8 @@ struct Kin {
     int ok;     // bit c: component c has J > 0
 };
 
-template <int D, class V>
+// BF: ln J by the branch-free FP32 logarithm (vlog1p_bf) instead of vlog1p
+template <int D, class V, bool BF = false>
 __device__ __forceinline__ void kinematics(const V (&H)[D][D], Kin<D, V>& k) {
     using S = typename VT<V>::S;
     const V one = splat<V>(S(1));
@@ -47,7 +48,10 @@ __device__ __forceinline__ void kinematics(const V (&H)[D][D], Kin<D, V>& k) {
         k.G[0][1] = H[1][0] * nrJ;
         k.G[1][0] = H[0][1] * nrJ;
         k.G[1][1] = (detH + H[1][1]) * nrJ;
-        k.lnJ = vlog1p(vsel(k.ok, Jm1, S(0)));
+        if constexpr (BF)
+            k.lnJ = vlog1p_bf(vsel(k.ok, Jm1, S(0)));
+        else
+            k.lnJ = vlog1p(vsel(k.ok, Jm1, S(0)));
     } else {
         V c[3][3];
         c[0][0] = vfma(H[1][1], H[2][2], -(H[1][2] * H[2][1]));
@@ -76,7 +80,10 @@ __device__ __forceinline__ void kinematics(const V (&H)[D][D], Kin<D, V>& k) {
                 if (i == j) x = x - s;
                 k.G[i][j] = x * rJ;
             }
-        k.lnJ = vlog1p(vsel(k.ok, Jm1, S(0)));
+        if constexpr (BF)
+            k.lnJ = vlog1p_bf(vsel(k.ok, Jm1, S(0)));
+        else
+            k.lnJ = vlog1p(vsel(k.ok, Jm1, S(0)));
     }
 }
 

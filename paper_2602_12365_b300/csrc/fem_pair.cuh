@@ -1,0 +1,449 @@
+// Pair kernels: the FP32 residual and HVP of P1 elements (Algorithm 1:
+// gather, field gradient, Neo-Hookean stress or tangent action, scatter)
+// with every lane computing TWO elements at once, one from each of two rounds,
+// in the two halves of the paired FP32 instructions of sm_100+ (fma.rn.f32x2:
+// one issue slot for two FMAs).  The tet residual and HVP are bound by
+// instruction issue, not by HBM (at the HBM floor an SM can issue about 330
+// warp instructions per round of 32 elements, the one-element kernel needs
+// about 500), and the element arithmetic is ~60 % of their instructions: two
+// elements per instruction remove most of it.
+//
+// Work decomposition as the tile kernel (fem_kernels.cuh): one CTA per tile,
+// kWarps warps, per-warp accumulator copies, node buffers double-buffered
+// and gathered a tile ahead, shared nodes through partial slots and the
+// finalize kernel, every sum in a fixed order (bitwise reproducible).  What
+// differs:
+//   records  a PAIR record holds two rounds of a warp's range (A = rounds
+//            r0 + 2k, B = r0 + 2k + 1; an odd range ends with an empty B):
+//            per lane one 16-byte chunk of node ids (A's then B's), then the
+//            geometry as (A, B) pairs in 16-byte chunks (grad N and w det J:
+//            pair j of a lane at chunk j / 2), then (mu_A, mu_B, lam_A,
+//            lam_B) when the moduli vary per element.  A 16-byte load gives
+//            two ready pairs, so the paired arithmetic needs no packing.
+//   empty    lanes without an element name a dummy node (index max_nlp, zero
+//            in both node buffers) and carry zero geometry, so they compute
+//            zero contributions with no branch; the dummy accumulator entry
+//            is never read back.
+//   math     one straight-line block per pair: no data-dependent branch (the
+//            branch-free FP32 logarithm of fem_vec.cuh).
+// The scatter adds A's contributions (low halves) for all lanes, then B's
+// (high halves): the lanes of one round share no node, and the warp
+// synchronises between the two rounds.
+#pragma once
+#include "fem_kernels.cuh"
+
+namespace fem {
+
+// pairs of a tile of R rounds: warp w runs the pair_rounds(R, w) consecutive
+// rounds after those of the warps before it (the tile kernel's split) as
+// pair_count(R, w) pairs, starting at pair pair_first(R, w) of the tile
+__host__ __device__ inline int pair_rounds(int R, int w) { return R / kWarps + (w < R % kWarps ? 1 : 0); }
+__host__ __device__ inline int pair_count(int R, int w) { return (pair_rounds(R, w) + 1) / 2; }
+__host__ __device__ inline int pair_first(int R, int w) {
+    int f = 0;
+    for (int v = 0; v < w; ++v) f += pair_count(R, v);
+    return f;
+}
+
+template <int ET>
+struct PairT;
+template <>
+struct PairT<0> {  // P1 triangle, plane strain: grad N_0, grad N_1, w det J
+    static constexpr int D = 2, NEN = 3, NG = 5, NCH = 3;
+};
+template <>
+struct PairT<1> {  // P1 tetrahedron: grad N_0..grad N_2, w det J
+    static constexpr int D = 3, NEN = 4, NG = 10, NCH = 5;
+};
+
+// bytes of one pair record: ids, geometry pairs, optional moduli
+__host__ __device__ constexpr int pair_rec_bytes(int et, bool mat) {
+    return 32 * 16 * (1 + (et == 0 ? 3 : 5) + (mat ? 1 : 0));
+}
+
+struct PairLayout {
+    int off_v, buf_bytes, off_buf0, off_buf1, off_acc, acc_stride, off_red, off_tab, off_tabp, off_ring, off_bar, total;
+};
+
+// node buffers hold max_nlp + 1 entries (the last is the dummy node)
+__host__ __device__ inline PairLayout pair_layout(int et, int op, int max_nlp, int prec_bytes) {
+    const int vw = et == 0 ? 2 : 4;
+    const int nodes = max_nlp + 1;
+    PairLayout L;
+    L.off_v = align16(nodes * vw * 4);
+    L.buf_bytes = align16(op == OP_HVP ? 2 * L.off_v : L.off_v);
+    L.off_buf0 = 0;
+    L.off_buf1 = L.buf_bytes;
+    int o = 2 * L.buf_bytes;
+    // per-warp accumulator copies at a 16-byte stride (acc_stride floats),
+    // so that every copy starts on a 16-byte boundary for vector stores
+    L.off_acc = o;
+    L.acc_stride = align16(nodes * vw * 4) / 4;
+    o += kWarps * L.acc_stride * 4;
+    L.off_red = o;  // the CTA's status flags
+    o = align16(o + 16);
+    L.off_tab = o;
+    o = align16(o + kMaxTilesPerCta * 16);
+    L.off_tabp = o;
+    o = align16(o + kMaxTilesPerCta * 4);
+    L.off_ring = o = align16(o);
+    o += kWarps * prec_bytes;
+    L.off_bar = o = align16(o);
+    o += kWarps * 8;
+    L.total = align16(o);
+    return L;
+}
+
+// pair j of a lane from its geometry chunks
+__device__ __forceinline__ F2 pair_of(const float4 (&gc)[5], int j) {
+    const float4 c = gc[j >> 1];
+    return (j & 1) ? mk2(c.z, c.w) : mk2(c.x, c.y);
+}
+
+template <int ET, int OP>
+__device__ __forceinline__ void pair_body(const KParams& p) {
+    using PT = PairT<ET>;
+    constexpr int D = PT::D, NEN = PT::NEN, NM1 = NEN - 1, NG = PT::NG, NCH = PT::NCH;
+    constexpr int VW = D == 2 ? 2 : 4;
+    constexpr bool kHvp = OP == OP_HVP;
+    static_assert(OP == OP_RESIDUAL || OP == OP_HVP, "pair kernels: residual and HVP");
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
+    if (n_my == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PairLayout L = pair_layout(ET, OP, p.max_nlp, p.prec_bytes);
+    const int nodes = p.max_nlp + 1;
+    float* sAcc = reinterpret_cast<float*>(smem + L.off_acc);
+    int* sFlag = reinterpret_cast<int*>(smem + L.off_red);
+    int4* tab = reinterpret_cast<int4*>(smem + L.off_tab);  // (node begin, padded count, round begin, rounds)
+    int* tabp = reinterpret_cast<int*>(smem + L.off_tabp);  // first pair record of the tile
+    uint8_t* ring = smem + L.off_ring + warp * p.prec_bytes;
+    uint64_t* rbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp;
+    auto bufU = [&](int b) { return reinterpret_cast<float*>(smem + (b ? L.off_buf1 : L.off_buf0)); };
+    auto bufV = [&](int b) { return reinterpret_cast<float*>(smem + (b ? L.off_buf1 : L.off_buf0) + L.off_v); };
+    const float* gu = static_cast<const float*>(p.u);
+    const float* gv = static_cast<const float*>(p.v);
+    const float mu0 = (float)p.mu0, lam0 = (float)p.lam0;
+    int flags_local = 0;
+
+    // 0. tile table, barriers, the dummy node (zero in both buffers)
+    for (int i = tid; i < n_my; i += kThreads) {
+        const int t = cta + i * G;
+        const int64_t n0 = p.tile_node_ptr[t], n1 = p.tile_node_ptr[t + 1];
+        const int r0 = p.tile_round_ptr[t], r1 = p.tile_round_ptr[t + 1];
+        tab[i] = make_int4((int)n0, (int)(n1 - n0), r0, r1 - r0);
+        tabp[i] = p.tile_pair_ptr[t];
+    }
+    if (tid == 0) {
+        for (int k = 0; k < kWarps; ++k) mbar_init(reinterpret_cast<uint64_t*>(smem + L.off_bar) + k, 1);
+        *sFlag = 0;
+        fence_mbar_init();
+    }
+    if (tid < 2 * VW) {
+        const int b = tid / VW, c = tid % VW;
+        bufU(b)[(nodes - 1) * VW + c] = 0.f;
+        if constexpr (kHvp) bufV(b)[(nodes - 1) * VW + c] = 0.f;
+    }
+    __syncthreads();
+
+    // node metadata (global id, partial slot, Dirichlet bits) of the current
+    // and the next tile in registers, a tile ahead of its use
+    constexpr int kMeta = 4;
+    struct Meta {
+        int g[kMeta], s[kMeta];
+        uint32_t m;
+    };
+    auto load_meta = [&](int i, Meta& M) {
+        const int4 tb = tab[i];
+        M.m = 0u;
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k) {
+            const int j = tid + kThreads * k;
+            M.g[k] = -1;
+            M.s[k] = -1;
+            if (j < tb.y) {
+                M.g[k] = __ldg(p.node_gid + tb.x + j);
+                M.s[k] = __ldg(p.node_slot + tb.x + j);
+                M.m |= (uint32_t)__ldg(p.node_mask_local + tb.x + j) << (8 * k);
+            }
+        }
+    };
+    // gather tile i's nodal values into buffer i & 1 (all threads, cp.async)
+    auto gather = [&](int i, const Meta& M) {
+        const int4 tb = tab[i];
+        float* bu = bufU(i & 1);
+        float* bv = bufV(i & 1);
+        auto one = [&](int j, int64_t g) {
+            if (g < 0) return;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                cp_async<4>(bu + j * VW + c, gu + g * D + c);
+                if constexpr (kHvp) cp_async<4>(bv + j * VW + c, gv + g * D + c);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k)
+            if (tid + kThreads * k < tb.y) one(tid + kThreads * k, M.g[k]);
+        for (int j = tid + kThreads * kMeta; j < tb.y; j += kThreads) one(j, __ldg(p.node_gid + tb.x + j));
+        cp_async_commit();
+    };
+    // this warp's pair records of tile i: warp w runs the rounds
+    // [r0 + w q + min(w, R % kWarps), ...), n_w = q + (w < R % kWarps), q = R / kWarps,
+    // as ceil(n_w / 2) pairs; the tile's pairs are stored warp by warp
+    auto my_pairs = [&](int i, int& p0, int& np) {
+        const int R = tab[i].w;
+        p0 = tabp[i] + pair_first(R, warp);
+        np = pair_count(R, warp);
+    };
+    // ring producer (lane 0): one pair record per stage, across tiles
+    // ring producer (lane 0): a cursor over the warp's pair records across
+    // its tiles gives the next record index (-1 past the last); one record
+    // per copy, one stage per warp
+    struct Cursor {
+        int i, it, p0, np;
+    };
+    auto next_rec = [&](Cursor& q) -> int64_t {
+        while (q.it >= q.np) {
+            if (++q.i >= n_my) return -1;
+            q.it = 0;
+            my_pairs(q.i, q.p0, q.np);
+        }
+        return (int64_t)(q.p0 + q.it++);
+    };
+    Cursor cc{0, 0, 0, 0};
+    my_pairs(0, cc.p0, cc.np);
+    int issued = 0;
+    auto issue_next = [&]() {
+        const int64_t r = next_rec(cc);
+        if (r < 0) return;
+        bulk_load(ring, p.prec + r * p.prec_bytes, (uint32_t)p.prec_bytes, rbar);
+        ++issued;
+    };
+
+    // 1. start (up to the wait, only mesh data is read: programmatic
+    // dependent launch)
+    Meta cur, nxt;
+    load_meta(0, cur);
+    if (n_my > 1) load_meta(1, nxt);
+    grid_dependency_wait();
+    if (p.skip != nullptr && *p.skip != 0) return;
+    if (lane == 0) issue_next();
+    gather(0, cur);
+
+    int consumed = 0;
+    bool timed_out = false;
+    int inv = 0;
+    for (int i = 0; i < n_my; ++i) {
+        float* sU = bufU(i & 1);
+        float* sV = bufV(i & 1);
+        const int nlp = tab[i].y;
+        const int64_t nbase = tab[i].x;
+        cp_async_wait_all();
+        __syncthreads();
+        // 2. fix-ups of the gathered values (finite inputs; the HVP's input
+        // mask); zero the accumulators
+        auto fixup = [&](int j, int g, uint32_t m) {
+            if (g < 0) return;
+            bool fin = true;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                fin = fin && finite_(sU[j * VW + c]);
+                if constexpr (kHvp) {
+                    if ((p.flags & 2u) && ((m >> c) & 1)) sV[j * VW + c] = 0.f;
+                    fin = fin && finite_(sV[j * VW + c]);
+                }
+            }
+            if (!fin) flags_local |= 2;
+        };
+#pragma unroll
+        for (int k = 0; k < kMeta; ++k)
+            if (tid + kThreads * k < nlp) fixup(tid + kThreads * k, cur.g[k], (cur.m >> (8 * k)) & 0xffu);
+        for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
+            fixup(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_mask_local + nbase + j));
+        {
+            float* myz = sAcc + (size_t)warp * L.acc_stride;
+            float4* z = reinterpret_cast<float4*>(myz);
+            const int nz = (nlp * VW + 3) / 4;
+            for (int j = lane; j < nz; j += 32) z[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+
+        // 3. pairs of rounds
+        int p0, np;
+        my_pairs(i, p0, np);
+        float* myAcc = sAcc + (size_t)warp * L.acc_stride;
+        bool gathered = (i + 1 >= n_my);
+        for (int k = 0; k < np && !timed_out; ++k) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(rbar, (uint32_t)(consumed & 1)))) {
+                timed_out = true;  // warp-uniform
+                break;
+            }
+            ++consumed;
+            const uint8_t* st = ring;
+            const uint4 cw = reinterpret_cast<const uint4*>(st)[lane];
+            float4 gc[5];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) gc[c] = reinterpret_cast<const float4*>(st + 512 * (1 + c))[lane];
+#pragma unroll
+            for (int c = NCH; c < 5; ++c) gc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 mc = p.has_mat ? reinterpret_cast<const float4*>(st + 512 * (1 + NCH))[lane]
+                                        : make_float4(mu0, mu0, lam0, lam0);
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_next();
+            }
+            if (!gathered) {  // the next tile's nodes, spread over all threads
+                gather(i + 1, nxt);
+                gathered = true;
+            }
+            int ia[NEN], ib[NEN];
+            if constexpr (NEN == 4) {
+                ia[0] = cw.x & 0xffff, ia[1] = cw.x >> 16, ia[2] = cw.y & 0xffff, ia[3] = cw.y >> 16;
+                ib[0] = cw.z & 0xffff, ib[1] = cw.z >> 16, ib[2] = cw.w & 0xffff, ib[3] = cw.w >> 16;
+            } else {
+                ia[0] = cw.x & 0xffff, ia[1] = cw.x >> 16, ia[2] = cw.y & 0xffff;
+                ib[0] = cw.z & 0xffff, ib[1] = cw.z >> 16, ib[2] = cw.w & 0xffff;
+            }
+            // gather and differences against the reference (last) node: the
+            // scalar differences land in the two halves of the pairs
+            F2 du[NM1][D], dv[NM1][D];
+            {
+                float ta[NEN][4], tb[NEN][4];
+#pragma unroll
+                for (int a = 0; a < NEN; ++a) {
+                    lds_vec<VW, float>(sU, ia[a], ta[a]);
+                    lds_vec<VW, float>(sU, ib[a], tb[a]);
+                }
+#pragma unroll
+                for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) du[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
+                if constexpr (kHvp) {
+#pragma unroll
+                    for (int a = 0; a < NEN; ++a) {
+                        lds_vec<VW, float>(sV, ia[a], ta[a]);
+                        lds_vec<VW, float>(sV, ib[a], tb[a]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                        for (int c = 0; c < D; ++c) dv[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
+                }
+            }
+            F2 g[NM1][D];
+#pragma unroll
+            for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                for (int c = 0; c < D; ++c) g[a][c] = pair_of(gc, a * D + c);
+            F2 wdJ = pair_of(gc, NG - 1);
+            F2 H[D][D];
+            outer_sum<D, F2>(du, g, NM1, H);
+            Kin<D, F2> kin;
+            kinematics<D, F2, true>(H, kin);
+            const int bad = 3 & ~kin.ok;  // empty halves have H = 0, J = 1
+            inv |= bad;
+            wdJ = vsel(kin.ok, wdJ, 0.f);  // inverted halves contribute nothing
+            const F2 wmu = wdJ * mk2(mc.x, mc.y), wlam = wdJ * mk2(mc.z, mc.w);
+            F2 P[D][D];
+            if constexpr (kHvp) {
+                F2 dF[D][D];
+                outer_sum<D, F2>(dv, g, NM1, dF);
+                tangent<D, F2>(dF, kin, wmu, wlam, P);
+            } else {
+                stress<D, F2>(H, kin, wmu, wlam, P);
+            }
+            F2 f[NEN][D];
+#pragma unroll
+            for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    F2 s = P[c][0] * g[a][0];
+#pragma unroll
+                    for (int j = 1; j < D; ++j) s = vfma(P[c][j], g[a][j], s);
+                    f[a][c] = s;
+                }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                F2 s = -f[0][c];
+#pragma unroll
+                for (int a = 1; a < NM1; ++a) s = s - f[a][c];
+                f[NM1][c] = s;
+            }
+            // scatter round A (low halves), then round B (high halves).  The
+            // lanes of one round hit distinct nodes of the warp's own copy, so
+            // the adds of a node come in round order (fixed, reproducible)
+            auto scatter = [&](const int (&id)[NEN], int h) {
+#pragma unroll
+                for (int a = 0; a < NEN; ++a) {
+                    float cur4[4];
+                    lds_vec<VW, float>(myAcc, id[a], cur4);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) cur4[c] += vcomp(f[a][c], h);
+                    // a fresh padding value keeps the store one 16-byte access
+                    if constexpr (VW > D) cur4[VW - 1] = 0.f;
+                    sts_vec<VW, float>(myAcc, id[a], cur4);
+                }
+            };
+            scatter(ia, 0);
+            __syncwarp();
+            scatter(ib, 1);
+            __syncwarp();
+        }
+        if (!gathered && !timed_out) gather(i + 1, nxt);  // a warp without pairs in this tile
+        __syncthreads();
+
+        // 4. combine the warp copies in warp order; private nodes to the
+        // output, shared nodes to their partial slot
+        {
+            float* part = static_cast<float*>(p.partial);
+            float* out = static_cast<float*>(p.out);
+            auto combine = [&](int j, int g, int slot, uint32_t msk) {
+                if (g < 0) return;
+                float sum[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    float tv[4];
+                    lds_vec<VW, float>(sAcc + (size_t)w * L.acc_stride, j, tv);
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) sum[c] += tv[c];
+                }
+                if (slot < 0)
+                    flags_local |= write_vec<D, float>(out, g, sum, (uint8_t)msk, p.flags);
+                else
+                    sts_vec<VW, float>(part, slot, sum);
+            };
+#pragma unroll
+            for (int k = 0; k < kMeta; ++k)
+                if (tid + kThreads * k < nlp) combine(tid + kThreads * k, cur.g[k], cur.s[k], (cur.m >> (8 * k)) & 0xffu);
+            for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
+                combine(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_slot + nbase + j),
+                        __ldg(p.node_mask_local + nbase + j));
+        }
+        __syncthreads();
+        cur = nxt;
+        if (i + 2 < n_my) load_meta(i + 2, nxt);
+    }
+    if (timed_out) flags_local |= 4;
+    // drain the copy still in flight before the CTA may exit
+    if (lane == 0)
+        for (int j = consumed; j < issued; ++j) mbar_wait_bounded(rbar, (uint32_t)(j & 1));
+    cp_async_wait_all();
+    if (inv) flags_local |= 1;
+    {
+        const int wf = __reduce_or_sync(0xffffffffu, flags_local);
+        if (lane == 0 && wf) atomicOr(sFlag, wf);
+    }
+    __syncthreads();
+    if (tid == 0 && *sFlag) atomicOr(p.status, *sFlag);
+}
+
+// four CTAs of kThreads per SM: at most 128 registers per thread
+template <int ET, int OP>
+__global__ void __launch_bounds__(kThreads, 4) pair_kernel(const KParams p) {
+    pair_body<ET, OP>(p);
+}
+
+}  // namespace fem

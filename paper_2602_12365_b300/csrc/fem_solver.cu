@@ -600,8 +600,91 @@ __global__ void trial_point(int64_t n, const double* u, double alpha, const T* x
 // Minv_n = D_n^-1 through the Cholesky factor D_n = L L^T (FP64 per node):
 // L^-1 by forward substitution, Minv = L^-T L^-1.  A non-positive pivot sets
 // *bad and leaves the identity.
+// uc = u on prescribed components, 0 on free ones
+template <int D>
+__global__ void prescribed_part(int64_t nn, const uint8_t* mask, const double* u, double* uc) {
+    for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+        const uint8_t m = mask[n];
+#pragma unroll
+        for (int c = 0; c < D; ++c) uc[n * D + c] = ((m >> c) & 1) ? u[n * D + c] : 0.0;
+    }
+}
+
+// a = uc - lam (the adjoint weights: u_c on prescribed DOFs, -lam on free
+// ones, where lam vanishes on prescribed DOFs), FP64 and optionally FP32
+__global__ void adjoint_weights(int64_t n, const double* uc, const double* lam, double* a, float* a32) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT) {
+        const double x = uc[i] - lam[i];
+        a[i] = x;
+        if (a32) a32[i] = (float)x;
+    }
+}
+
+// res = rhs - res (res holds M K M lam on entry)
+__global__ void residual_update(int64_t n, const double* rhs, double* res) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        res[i] = rhs[i] - res[i];
+}
+
+// y += x
+__global__ void add_into(int64_t n, const double* x, double* y) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT) y[i] += x[i];
+}
+
+// g = g_mu + ratio g_lam per element (lambda_e = ratio mu_e)
+__global__ void tied_moduli(int64_t n, double* g, const double* glam, double ratio) {
+    for (int64_t i = blockIdx.x * (int64_t)kVT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVT)
+        g[i] = fma(ratio, glam[i], g[i]);
+}
+
 template <int D, typename T>
 __global__ void block_jacobi_inverse(int64_t nn, const T* Db, T* Minv, int* bad) {
+    if constexpr (sizeof(T) == 4) {
+        // FP32 CG: the closed-form inverse adj(A) / det A in FP32, with the
+        // block called SPD when its leading principal minors are positive
+        // (Sylvester's criterion); the nodal blocks are symmetric and well
+        // conditioned, so FP32 rounding changes the preconditioner, not the
+        // converged solution
+        for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
+            float A[D][D], Mi[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) A[i][j] = (float)Db[n * D * D + i * D + j];
+            float det, m2;
+            if constexpr (D == 3) {
+                const float c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+                const float c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+                const float c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+                m2 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+                det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+                const float rd = 1.0f / det;
+                Mi[0][0] = c00 * rd;
+                Mi[1][0] = c01 * rd;
+                Mi[2][0] = c02 * rd;
+                Mi[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * rd;
+                Mi[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * rd;
+                Mi[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * rd;
+                Mi[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * rd;
+                Mi[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * rd;
+                Mi[2][2] = m2 * rd;
+            } else {
+                m2 = A[0][0];
+                det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+                const float rd = 1.0f / det;
+                Mi[0][0] = A[1][1] * rd;
+                Mi[0][1] = -A[0][1] * rd;
+                Mi[1][0] = -A[1][0] * rd;
+                Mi[1][1] = A[0][0] * rd;
+            }
+            const bool ok = A[0][0] > 0.f && m2 > 0.f && det > 0.f && isfinite(det);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) Minv[n * D * D + i * D + j] = ok ? Mi[i][j] : (i == j ? 1.f : 0.f);
+            if (!ok) atomicOr(bad, 1);
+        }
+    } else {
     for (int64_t n = blockIdx.x * (int64_t)kVT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVT) {
         double A[D][D], L[D][D] = {}, Li[D][D] = {};
 #pragma unroll
@@ -646,6 +729,7 @@ __global__ void block_jacobi_inverse(int64_t nn, const T* Db, T* Minv, int* bad)
             }
         if (!ok) atomicOr(bad, 1);
     }
+    }
 }
 
 int grid_for(int64_t work) {
@@ -687,6 +771,8 @@ struct SolverWork {
     CgState* cg = nullptr;
     DotState* dot = nullptr;
     double* scal = nullptr;  // energy output (4 doubles)
+    double* glam = nullptr;  // compliance gradient: per-element g_lam (allocated on first use)
+    double* adj = nullptr;   // compliance gradient: correction of the refined adjoint solve
     int* bad = nullptr;
     // pinned host mirror
     struct Host {
@@ -1265,6 +1351,100 @@ fem_status fem_tangent_solve(fem_mesh* m, int cg_dtype, const double* u, const d
     if (rc == 5) return fail(FEM_ERR_NOT_SPD, "fem_tangent_solve: a nodal diagonal block is not SPD");
     if (rc == 2) return fail(FEM_ERR_NEG_CURVATURE, "fem_tangent_solve: p^T K p <= 0 (K is not positive definite)");
     if (rc == 3) return fail(FEM_ERR_NOT_CONVERGED, "fem_tangent_solve: iteration cap reached");
+    return FEM_OK;
+}
+
+fem_status fem_compliance_gradient(fem_mesh* m, const double* u, double ratio, double rtol, int cg_dtype,
+                                   int vjp_dtype, double* dmu, double* c_dev, int64_t* iters, void* stream) {
+    if (!m || !u || !dmu || !c_dev) return fail(FEM_ERR_ARG, "null mesh, u, dmu or c");
+    if (cg_dtype != FEM_F64 && cg_dtype != FEM_F32) return fail(FEM_ERR_ARG, "cg_dtype must be FEM_F64 or FEM_F32");
+    if (vjp_dtype != FEM_F64 && vjp_dtype != FEM_F32) return fail(FEM_ERR_ARG, "vjp_dtype must be FEM_F64 or FEM_F32");
+    if ((cg_dtype == FEM_F32 || vjp_dtype == FEM_F32) && m->precision != FEM_PREC_MIXED)
+        return fail(FEM_ERR_ARG, "FEM_F32 needs a mesh created with FEM_PREC_MIXED");
+    if (!(rtol > 0.0) || !std::isfinite(ratio)) return fail(FEM_ERR_ARG, "need rtol > 0 and a finite ratio");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FEM_TRY(ensure_work(m, cg_dtype));
+    if (vjp_dtype == FEM_F32) FEM_TRY(ensure_work(m, FEM_F32));
+    SolverWork* w = m->solver;
+    if (!w->glam) FEM_TRY(dalloc(w, &w->glam, (size_t)m->info.n_elems));
+    const int gn = grid_for(w->nn), gd = grid_for(w->nd);
+    double* uc = w->du;   // prescribed part of u
+    double* r = w->r;     // unmasked residual at u
+    double* rhs = w->t;   // K_fc u_c (free rows)
+    double* lam = w->ut;  // adjoint solution
+    // 1. c = u_c^T r(u): the work of the prescribed displacements
+    if (m->dim == 2)
+        prescribed_part<2><<<gn, kVT, 0, st>>>(w->nn, m->node_mask, u, uc);
+    else
+        prescribed_part<3><<<gn, kVT, 0, st>>>(w->nn, m->node_mask, u, uc);
+    FEM_TRY(femi::run_op(m, FEM_F64, fem::OP_RESIDUAL, u, nullptr, r, nullptr, 0u, st, nullptr));
+    dot_kernel<double, double><<<gd, kVT, 0, st>>>(w->nd, uc, r, w->dot, w->partial);
+    CUDA_TRY(cudaMemcpyAsync(c_dev, &w->dot->value, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // 2. right-hand side K_fc u_c: an HVP with u_c as the direction, rows of
+    // the free DOFs only
+    FEM_TRY(femi::run_op(m, FEM_F64, fem::OP_HVP, u, uc, rhs, nullptr, (unsigned)FEM_MASK_OUT, st, nullptr));
+    // 3. adjoint solve K_ff lam = K_fc u_c (the PCG of the Newton step).  With
+    // an FP32 PCG the solve is refined in FP64 (mixed-precision iterative
+    // refinement): the FP64 residual rhs - M K M lam of the current lam is
+    // solved for a correction by the FP32 PCG to a modest tolerance, and added;
+    // the FP32 solve alone stalls near its own rounding level, far above
+    // rtol on fine meshes.
+    fem_newton_opts o;
+    fem_newton_default_opts(&o);
+    o.cg_dtype = cg_dtype;
+    fem_newton_stats stats{};
+    Stepper stepper(m, o, &stats, st);
+    fem_status err = FEM_OK;
+    int64_t it_total = 0;
+    auto solve = [&](const double* b, double* x, double tol) -> fem_status {
+        int64_t it = 0;
+        const int rc = stepper.tangent_solve(u, b, x, tol, &it, &err);
+        it_total += it;
+        if (err != FEM_OK) return err;
+        if (rc == 5) return fail(FEM_ERR_NOT_SPD, "fem_compliance_gradient: a nodal diagonal block is not SPD");
+        if (rc == 2) return fail(FEM_ERR_NEG_CURVATURE, "fem_compliance_gradient: p^T K p <= 0 in the adjoint solve");
+        if (rc == 3) return fail(FEM_ERR_NOT_CONVERGED, "fem_compliance_gradient: adjoint iteration cap reached");
+        return FEM_OK;
+    };
+    if (cg_dtype == FEM_F64) {
+        FEM_TRY(solve(rhs, lam, rtol));
+    } else {
+        constexpr double kInner = 1e-4;  // FP32 PCG tolerance of each correction
+        constexpr int kMaxRefine = 8;
+        double* res = r;  // the residual vector is free again once c is copied out
+        if (!w->adj) FEM_TRY(dalloc(w, &w->adj, (size_t)w->nd));
+        double* dlam = w->adj;
+        double bb = 0.0;
+        dot_kernel<double, double><<<gd, kVT, 0, st>>>(w->nd, rhs, rhs, w->dot, w->partial);
+        CUDA_TRY(cudaMemcpyAsync(&w->h->dot, w->dot, sizeof(DotState), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        bb = w->h->dot.value;
+        FEM_TRY(solve(rhs, lam, kInner));
+        for (int k = 0; k < kMaxRefine; ++k) {
+            // res = rhs - M K M lam (FP64)
+            FEM_TRY(femi::run_op(m, FEM_F64, fem::OP_HVP, u, lam, res, nullptr, (unsigned)FEM_MASK_BOTH, st, nullptr));
+            residual_update<<<gd, kVT, 0, st>>>(w->nd, rhs, res);
+            dot_kernel<double, double><<<gd, kVT, 0, st>>>(w->nd, res, res, w->dot, w->partial);
+            CUDA_TRY(cudaMemcpyAsync(&w->h->dot, w->dot, sizeof(DotState), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            const double rr = w->h->dot.value;
+            if (!(rr > rtol * rtol * bb)) break;
+            FEM_TRY(solve(res, dlam, kInner));
+            add_into<<<gd, kVT, 0, st>>>(w->nd, dlam, lam);
+        }
+    }
+    if (iters) *iters = it_total;
+    // 4. a = u_c - lam; dc/dmu_e = a^T (dr_e/dmu_e + ratio dr_e/dlambda_e)
+    const bool f32 = vjp_dtype == FEM_F32;
+    adjoint_weights<<<gd, kVT, 0, st>>>(w->nd, uc, lam, uc, f32 ? w->du32 : nullptr);
+    if (f32) {
+        to_f32<<<gd, kVT, 0, st>>>(w->nd, u, w->u32);
+        FEM_TRY(fem_param_vjp(m, FEM_F32, w->u32, w->du32, dmu, w->glam, st));
+    } else {
+        FEM_TRY(fem_param_vjp(m, FEM_F64, u, uc, dmu, w->glam, st));
+    }
+    tied_moduli<<<grid_for(m->info.n_elems), kVT, 0, st>>>(m->info.n_elems, dmu, w->glam, ratio);
+    CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 

@@ -321,7 +321,41 @@ class Mesh:
                                           C.byref(it), _stream(stream)))
         return x, it.value
 
+    def set_moduli(self, mu, lam, stream=None):
+        """Replace the per-element moduli (host arrays, element order)."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(-1)
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+        if mu.size != self.n_el or lam.size != self.n_el:
+            raise ValueError("mu and lam need one value per element")
+        L.check(L.lib().fem_mesh_set_moduli(self._h, mu.ctypes.data_as(C.c_void_p), lam.ctypes.data_as(C.c_void_p),
+                                            _stream(stream)))
+
+    def compliance_gradient(self, u, ratio=10.0, rtol=1e-10, cg_dtype=torch.float64, vjp_dtype=torch.float64,
+                            stream=None):
+        """(c, dc/dmu [n_elems] FP64, adjoint PCG iterations) at the converged
+        FP64 state u, all of it in the library (fem_compliance_gradient)."""
+        if u.dtype != torch.float64:
+            raise TypeError("u must be float64 (the master state is FP64)")
+        self._check_vec(u)
+        g = torch.empty(self.n_el, dtype=torch.float64, device=u.device)
+        c = torch.empty(1, dtype=torch.float64, device=u.device)
+        it = C.c_int64(0)
+        code = {torch.float64: L.FEM_F64, torch.float32: L.FEM_F32}
+        L.check(L.lib().fem_compliance_gradient(self._h, _ptr(u), float(ratio), float(rtol), code[cg_dtype],
+                                                code[vjp_dtype], _ptr(g), _ptr(c), C.byref(it), _stream(stream)))
+        return c, g, it.value
+
     def sync_status(self, stream=None) -> int:
         f = C.c_int32(0)
         L.check(L.lib().fem_sync_status(self._h, _stream(stream), C.byref(f)))
         return f.value
+
+
+def fp32_fma_rate(blocks, iters, out, stream=None):
+    """Enqueue the FP32 FMA throughput kernel (fem_fp32_fma_rate) writing
+    `out` (device float32 [blocks * 256]); returns its FLOP count."""
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() < blocks * 256:
+        raise ValueError("out must be a CUDA float32 tensor of at least blocks * 256 elements")
+    fl = C.c_double(0.0)
+    L.check(L.lib().fem_fp32_fma_rate(int(blocks), int(iters), _ptr(out), C.byref(fl), _stream(stream)))
+    return fl.value

@@ -87,3 +87,22 @@ def test_static_rejects_a_mesh_over_the_limit():
     assert torch.equal(out, torch.full_like(out, 7.0))  # nothing enqueued
     # the regular entry point still serves this mesh
     assert torch.isfinite(gm.energy(u)[0])
+
+
+def test_static_rejects_a_bad_dtype_before_touching_the_shared_array():
+    # An FP32 call on a mesh built without FP32 records is refused before it
+    # touches the shared array: a static call of another handle queued just
+    # before it on the same stream keeps its arrival counter and its result.
+    m = mg.workload_tet(6, seed=8)
+    g64 = Mesh.from_fixture(m, precision="fp64", tile_elems=64)
+    gmx = Mesh.from_fixture(m, tile_elems=64)
+    u64, _ = _states(m, torch.float64)
+    ref = gmx.energy(u64).clone()
+    torch.cuda.synchronize()
+    first = gmx.energy_static(u64)  # queued, not yet synchronised
+    with pytest.raises(FemError, match="FEM_F32"):
+        g64.energy_static(u64.float())
+    second = gmx.energy_static(u64)
+    torch.cuda.synchronize()
+    assert torch.equal(first, ref) and torch.equal(second, ref)
+    assert g64.sync_status() == 0 and gmx.sync_status() == 0
