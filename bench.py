@@ -13,12 +13,18 @@ L2 (126 MB) is flushed before every timed step by writing a 256 MB buffer and
 then reading another 256 MB one (so the flush's dirty lines are written back
 before the timed kernels start); each step is timed with CUDA events on the
 stream the kernels run on.
-The line also carries the Newton-CG measurement ("newton"): seconds per load
-step to relative residual 1e-8 on the 64^3 random-moduli tet mesh, FP64
-against mixed precision (FP32 CG with FP64 dots, FP64 residual and energy),
-with block-Jacobi PCG, and mixed precision with the learned block
-preconditioner (weights trained on seeds 1-16 of the same mesh family).
-`--impl reference` times the FP64 CPU oracle instead (the reference arm).
+The line also carries: the same step warm (L2 not flushed, "warm"); the
+Newton-CG measurement ("newton"): seconds per load step to relative residual
+1e-8 on the 64^3 random-moduli tet family, every load step of the 20-step
+path on seeds 101-104, FP64 against mixed precision (FP32 CG with FP64 dots,
+FP64 residual and energy) with block-Jacobi PCG, and mixed precision with the
+learned block preconditioner (weights trained on seeds 1-16, so these seeds
+are unseen); the 128^3 Q1 hex workload ("hex128": residual and HVP against a
+measured FP32 FMA rate, and its mixed Newton-CG load path); the FP32 path's
+error against the FP64 path and the FP64 oracle at the benchmark's FP64 state
+("precision_error"); and the oracle on one pinned host core
+("cpu_baseline").  `--impl reference` times the FP64 CPU oracle instead (the
+reference arm).
 """
 from __future__ import annotations
 
@@ -55,8 +61,12 @@ def parse():
     ap.add_argument("--no-ncm", action="store_true", help="skip the neural-constitutive-model measurement")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the sparse-K (Algorithm 2) and atomic-scatter ablation measurements")
-    ap.add_argument("--newton-steps", type=int, default=2,
-                    help="load steps of the Newton-CG measurement per arm (0 = skip)")
+    ap.add_argument("--newton-steps", type=int, default=20,
+                    help="load steps of the Newton-CG measurement per arm and seed (0 = skip)")
+    ap.add_argument("--newton-seeds", default="101,102,103,104",
+                    help="mesh seeds of the Newton-CG measurement (the learned preconditioner's unseen seeds)")
+    ap.add_argument("--no-hex", action="store_true", help="skip the 128^3 Q1 hex measurement")
+    ap.add_argument("--hex-steps", type=int, default=10, help="load steps of the hex128 mixed Newton measurement")
     return ap.parse_args()
 
 
@@ -202,20 +212,6 @@ def config_dict(m, step, extra=None):
     return d
 
 
-def cpu_oracle_rate(m, u, v, reps=2):
-    """Oracle residual + HVP on the whole workload, single thread."""
-    import oracle
-    om = oracle.OracleMesh.from_mesh(m)
-    ts = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        om.residual(u)
-        om.hvp(u, v)
-        ts.append(time.perf_counter() - t0)
-    t = min(ts)
-    return m.n_el / t / 1e9, t
-
-
 def run_reference(args):
     world, rank, _ = dist_init(args)
     if rank != 0:
@@ -227,6 +223,12 @@ def run_reference(args):
     ne = m.n_el // 4
     sub = oracle.OracleMesh(m.elem_type, m.coords, m.conn[:ne], m.mu_e()[:ne], m.lam_e()[:ne],
                             m.dirichlet)
+    try:
+        core = min(os.sched_getaffinity(0))
+        os.sched_setaffinity(0, {core})
+        pinned = f"core {core} (sched_setaffinity, as taskset -c {core})"
+    except (AttributeError, OSError):
+        pinned = "not pinned"
     for _ in range(args.warmup):
         sub.residual(u)
         sub.hvp(u, v)
@@ -244,70 +246,199 @@ def run_reference(args):
             "config": config_dict(m, "1 residual + 1 HVP (FP64 CPU oracle, 1 thread)",
                                   {"sample": sample}),
             "cpu_baseline": {"value": val, "unit": "GElem/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_info()[0], "nproc": cpu_info()[1],
+                             "pinned": pinned},
             "e2e": {"value": val, "unit": "GElem/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-NEWTON_WORKLOAD = ("tet64 random moduli: 64^3 Kuhn tets (jitter seed 101), per-element mu "
-                   "lognormal(0, 0.5) (seed 101), lambda = 10 mu; base clamped, top compressed "
-                   "20 % in 20 load steps")
+NEWTON_WORKLOAD = ("tet64 random moduli (C4 family): 64^3 Kuhn tets (jitter seed = mesh seed), per-element mu "
+                   "lognormal(0, 0.5) (same seed), lambda = 10 mu; base clamped, top compressed 20 % in 20 load steps")
 
 
-def newton_arms(n, n_steps, dev):
-    """Seconds per Newton-CG load step (relative residual 1e-8), FP64 vs mixed
-    precision, block-Jacobi PCG, over the first n_steps of the 20-step path."""
+def newton_arms(n, n_steps, seeds, dev):
+    """Seconds per Newton-CG load step (relative residual 1e-8) on the 64^3
+    random-moduli tet family, per arm: FP64 block Jacobi, mixed precision
+    (FP32 CG, FP64 dots, FP64 residual and energy) with block Jacobi, and
+    mixed with the learned block preconditioner (weights trained on seeds
+    1-16 of the same family; the seeds here are unseen).  Every arm runs the
+    first n_steps load steps of the 20-step path on every seed; the headline
+    is the median over all those steps."""
     import torch
     from paper_2602_12365_b300 import meshgen as mg
     from paper_2602_12365_b300.fem import Mesh
-    m = mg.workload_tet(n, seed=101, random_moduli=101)
-    gm = Mesh.from_fixture(m, precision="mixed")
-    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
-    arms = [("fp64_block_jacobi", torch.float64, {}), ("mixed_block_jacobi", torch.float32, {})]
+    arms = [("fp64_block_jacobi", torch.float64, False), ("mixed_block_jacobi", torch.float32, False)]
     weights = os.path.join(ROOT, "paper_2602_12365_b300", "weights", "lp_tet64.npz")
+    lp = None
     if os.path.exists(weights):
         from paper_2602_12365_b300.learned import LearnedPreconditioner
-        arms.append(("mixed_learned", torch.float32, {"learned": LearnedPreconditioner.load(weights)}))
-    out, finals = {}, {}
-    for arm, dt, kw in arms:
-        u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device=dev)
-        # one-time setup outside the timing: the solver workspace (a step at
-        # rest returns at once) and, for the learned arm, the node graph
-        gm.newton_step(u, ubar, 0.0, 0.0, cg_dtype=dt, **kw)
-        if "learned" in kw:
-            kw["learned"].blocks(gm, u.float())
-        times, newton, cg = [], [], []
-        s_prev = 0.0
-        for k in range(1, n_steps + 1):
-            s = k / 20
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=dt, **kw)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b) * 1e-3)
-            newton.append(st["newton_iters"])
-            cg.append(st["cg_iters"])
-            s_prev = s
-        finals[arm] = u
-        out[arm] = {"s_per_load_step": statistics.median(times), "s_each": times,
-                    "newton_iters": newton, "cg_iters": cg}
-    ref = finals["fp64_block_jacobi"]
-    for arm, u in finals.items():
-        out[arm]["u_rel_diff_vs_fp64"] = float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref))
-    res = {"workload": NEWTON_WORKLOAD, "metric": "Newton-CG s/load step at relative residual 1e-8",
-           "load_steps": list(range(1, n_steps + 1)), "arms": out}
+        lp = LearnedPreconditioner.load(weights)
+        arms.append(("mixed_learned", torch.float32, True))
+    per = {a: {"s_each": [], "newton_iters": [], "cg_iters": [], "u_rel_diff_vs_fp64": [], "seeds": []}
+           for a, _, _ in arms}
+    for seed in seeds:
+        m = mg.workload_tet(n, seed=seed, random_moduli=seed)
+        gm = Mesh.from_fixture(m, precision="mixed")
+        ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device=dev)
+        finals = {}
+        for arm, dt, learned in arms:
+            kw = {"learned": lp} if learned else {}
+            u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device=dev)
+            # one-time setup outside the timing: the solver workspace (a step at
+            # rest returns at once) and, for the learned arm, the node graph
+            gm.newton_step(u, ubar, 0.0, 0.0, cg_dtype=dt, **kw)
+            if learned:
+                lp.blocks(gm, u.float())
+            s_prev = 0.0
+            times, newton, cg = [], [], []
+            for k in range(1, n_steps + 1):
+                s = k / 20
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=dt, **kw)
+                b.record(stream)
+                b.synchronize()
+                times.append(a.elapsed_time(b) * 1e-3)
+                newton.append(st["newton_iters"])
+                cg.append(st["cg_iters"])
+                s_prev = s
+            finals[arm] = u
+            per[arm]["s_each"].append(times)
+            per[arm]["newton_iters"].append(newton)
+            per[arm]["cg_iters"].append(cg)
+            per[arm]["seeds"].append(seed)
+        ref = finals["fp64_block_jacobi"]
+        for arm, u in finals.items():
+            per[arm]["u_rel_diff_vs_fp64"].append(float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref)))
+        del gm
+    out = {}
+    for arm, d in per.items():
+        flat = [t for ts in d["s_each"] for t in ts]
+        out[arm] = {"s_per_load_step": statistics.median(flat),
+                    "s_per_load_step_by_seed": [statistics.median(ts) for ts in d["s_each"]],
+                    "newton_iters_per_step_median": statistics.median(x for xs in d["newton_iters"] for x in xs),
+                    "cg_iters_per_step_median": statistics.median(x for xs in d["cg_iters"] for x in xs),
+                    "cg_iters_total_by_seed": [sum(xs) for xs in d["cg_iters"]],
+                    "u_rel_diff_vs_fp64_max": max(d["u_rel_diff_vs_fp64"]), **d}
+    res = {"workload": NEWTON_WORKLOAD, "metric": "Newton-CG s/load step at relative residual 1e-8 "
+                                                  "(median over every load step of every seed)",
+           "seeds": list(seeds), "load_steps": list(range(1, n_steps + 1)), "arms": out}
     t64 = out["fp64_block_jacobi"]["s_per_load_step"]
     for arm in out:
         if arm != "fp64_block_jacobi":
             res[f"speedup_{arm}_vs_fp64_block_jacobi"] = t64 / out[arm]["s_per_load_step"]
     if "mixed_learned" in out:
-        res["learned_weights"] = "paper_2602_12365_b300/weights/lp_tet64.npz (seeds 1-16, 20 load steps)"
+        res["learned_vs_mixed_block_jacobi"] = {
+            "time_ratio": out["mixed_learned"]["s_per_load_step"] / out["mixed_block_jacobi"]["s_per_load_step"],
+            "cg_iter_ratio": (sum(out["mixed_learned"]["cg_iters_total_by_seed"]) /
+                              sum(out["mixed_block_jacobi"]["cg_iters_total_by_seed"]))}
+        res["learned_weights"] = "paper_2602_12365_b300/weights/lp_tet64.npz (trained on seeds 1-16)"
     return res
+
+
+# FP32 flops per Q1 element of the hex operators (this formulation: J rebuilt
+# at each of the 8 Gauss points, FMA = 2), counted by ncu on a hex64 call
+# (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum, every
+# round full)
+HEX_FLOPS_RES = 4.69e3
+HEX_FLOPS_HVP = 6.57e3
+
+
+def fp32_peak(dev, clk=None):
+    """Measured FP32 FMA rate (TFLOP/s): the library's FMA-chain kernel on
+    8 blocks of 256 threads per SM, best of 5 (CUDA events)."""
+    import torch
+    from paper_2602_12365_b300 import fem
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = nsm * 8
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    fl = fem.fp32_fma_rate(blocks, 4096, out)
+    best = None
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fem.fp32_fma_rate(blocks, 4096, out)
+        b.record()
+        b.synchronize()
+        t = a.elapsed_time(b) * 1e-3
+        best = t if best is None else min(best, t)
+    return fl / best / 1e12
+
+
+def hex_arm(dev, flush_l2, steps, hex_steps):
+    """The 128^3 Q1 hex workload (C3): residual and HVP (FP32 element kernels,
+    L2 flushed before each call), their FP32 rate against the FMA rate
+    measured here and the nominal one, and the mixed-precision Newton-CG
+    seconds per load step over the 10-step shear path."""
+    import torch
+    from paper_2602_12365_b300 import meshgen as mg
+    from paper_2602_12365_b300.fem import Mesh
+    m = mg.workload_hex(128, seed=0)
+    gm = Mesh.from_fixture(m, precision="mixed")
+    ut = torch.as_tensor(mg.smooth_state(m, 0.5).ravel(), dtype=torch.float32, device=dev)
+    vt = torch.as_tensor(mg.random_direction(m, 1).ravel(), dtype=torch.float32, device=dev)
+    r, y = torch.empty_like(ut), torch.empty_like(ut)
+    for k in range(3):
+        flush_l2(k)
+        gm.residual(ut, out=r)
+        gm.hvp(ut, vt, out=y)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        flush_l2(k)
+        ev[k][0].record()
+        gm.residual(ut, out=r)
+        ev[k][1].record()
+        gm.hvp(ut, vt, out=y)
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    assert gm.sync_status() == 0
+    t_r = statistics.median(e[0].elapsed_time(e[1]) for e in ev) * 1e-3
+    t_h = statistics.median(e[1].elapsed_time(e[2]) for e in ev) * 1e-3
+    peak_meas = fp32_peak(dev)
+    props = torch.cuda.get_device_properties(dev)
+    nominal = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
+    tf_r = HEX_FLOPS_RES * m.n_el / t_r / 1e12
+    tf_h = HEX_FLOPS_HVP * m.n_el / t_h / 1e12
+    # the mixed Newton-CG load path (configs: base clamped, top shear 0.1 in 10 steps)
+    ubar = torch.as_tensor(m.ubar.ravel(), dtype=torch.float64, device=dev)
+    u = torch.zeros(m.n_nodes * 3, dtype=torch.float64, device=dev)
+    gm.newton_step(u, ubar, 0.0, 0.0, cg_dtype=torch.float32)  # workspace
+    times, newton, cg = [], [], []
+    s_prev = 0.0
+    for k in range(1, hex_steps + 1):
+        s = k / 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        st = gm.newton_step(u, ubar, s_prev, s, cg_dtype=torch.float32)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b) * 1e-3)
+        newton.append(st["newton_iters"])
+        cg.append(st["cg_iters"])
+        s_prev = s
+    return {"workload": "hex128: 128^3 Q1 hexahedra (2,097,152 elements, 2,146,689 nodes), 2x2x2 Gauss, "
+                        "per-element mu lognormal(0, 0.5) (seed 0), lambda = 10 mu; base clamped, top sheared",
+            "residual_us": t_r * 1e6, "hvp_us": t_h * 1e6,
+            "residual_gelem_s": m.n_el / t_r / 1e9, "hvp_gelem_s": m.n_el / t_h / 1e9,
+            "pair_gelem_s": m.n_el / (t_r + t_h) / 1e9,
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "flops_per_el": {"residual": HEX_FLOPS_RES,
+                                                                             "hvp": HEX_FLOPS_HVP},
+                         "achieved": {"residual": tf_r, "hvp": tf_h},
+                         "peak_measured": peak_meas, "peak_nominal": nominal,
+                         "frac_of_measured": {"residual": tf_r / peak_meas, "hvp": tf_h / peak_meas},
+                         "frac_of_nominal": {"residual": tf_r / nominal, "hvp": tf_h / nominal},
+                         "peak_how": "measured: fem_fp32_fma_rate (8 independent FMA chains per thread, 8 blocks "
+                                     "of 256 per SM, best of 5); nominal: SMs x 128 FP32 lanes x 2 x 2.032 GHz"},
+            "l2": "flushed before every call",
+            "newton_mixed": {"s_per_load_step": statistics.median(times), "s_each": times,
+                             "newton_iters": newton, "cg_iters": cg,
+                             "what": "mixed precision (FP32 CG with FP64 dots, FP64 residual and energy), block "
+                                     "Jacobi, relative residual 1e-8, top shear 0.1 in 10 load steps"}}
 
 
 def sparse_arm(gm, ut, vt, t_hvp_us, flush_l2, peak):
@@ -516,6 +647,21 @@ def run_ours(args):
             gm.hvp(ut, vt, out=y)
             ev[k][2].record(stream)
         torch.cuda.synchronize()
+    # warm: the same K steps with L2 not flushed (the step's inputs and the
+    # element stream partly L2-resident from the previous step)
+    ev_w = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda._sleep(int(2.0e9 * (0.5e-3 * args.steps + 2e-3)))
+    for k in range(args.steps):
+        ev_w[k][0].record(stream)
+        gm.residual(ut, out=r)
+        ev_w[k][1].record(stream)
+        gm.hvp(ut, vt, out=y)
+        ev_w[k][2].record(stream)
+    torch.cuda.synchronize()
+    warm = {"residual_us": statistics.median(e[0].elapsed_time(e[1]) for e in ev_w) * 1e3,
+            "hvp_us": statistics.median(e[1].elapsed_time(e[2]) for e in ev_w) * 1e3,
+            "l2": "not flushed (warm)"}
+    warm["pair_gelem_s"] = m.n_el / ((warm["residual_us"] + warm["hvp_us"]) * 1e-6) / 1e9
     barrier(world)
     t_step = max_over_ranks(sum(e[0].elapsed_time(e[2]) for e in ev_step) / args.steps, world, dev)
     t_res = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps  # ms
@@ -621,20 +767,101 @@ def run_ours(args):
     line["clocks"] = clk.summary()
     if e2e:
         line["e2e"] = e2e
+    line["warm"] = warm
     if not args.no_ncm and rank == 0:
         line["ncm"] = ncm_arm(m, gm, ut, vt, t_res * 1e3, t_hvp * 1e3, flush_l2, dev)
     if not args.no_sparse and rank == 0:  # per-GPU measurements, reported by rank 0
         line["atomic_ablation"] = atomic_arm(gm, ut, vt, t_res * 1e3, t_hvp * 1e3, flush_l2)
         line["sparse"] = sparse_arm(gm, ut, vt, t_hvp * 1e3, flush_l2, peak)
+    if not args.no_hex and rank == 0:
+        line["hex128"] = hex_arm(dev, flush_l2, min(args.steps, 20), args.hex_steps)
     if args.newton_steps > 0 and rank == 0:  # a per-GPU measurement, reported by rank 0
-        line["newton"] = newton_arms(args.n, args.newton_steps, dev)
+        seeds = [int(x) for x in args.newton_seeds.split(",") if x.strip()]
+        line["newton"] = newton_arms(args.n, args.newton_steps, seeds, dev)
+    # the FP32 path's results at the benchmark's FP64 state (u, v rounded to
+    # FP32 on the way in) against the FP64 path on the same GPU (the CPU leg
+    # below adds the oracle's own figures)
+    u64 = torch.as_tensor(u, dtype=torch.float64, device=dev)
+    v64 = torch.as_tensor(v, dtype=torch.float64, device=dev)
+    gm.residual(ut, out=r)  # the arms above reuse r and y
+    gm.hvp(ut, vt, out=y)
+    r64, y64 = gm.residual(u64), gm.hvp(u64, v64)
+    e32, e64 = gm.energy(ut), gm.energy(u64)
+    rel = lambda a, b: float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))  # noqa: E731
+    precision = {"state": "the benchmark's FP64 (u, v); FP32 calls receive them rounded to FP32",
+                 "residual_f32_vs_f64_gpu": rel(r, r64), "hvp_f32_vs_f64_gpu": rel(y, y64),
+                 "energy_f32_vs_f64_gpu": abs(float(e32[0]) - float(e64[0])) / abs(float(e64[0]))}
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, t = cpu_oracle_rate(m, u, v)
-        line["cpu_baseline"] = {"value": rate, "unit": "GElem/s", "cores": 1, "kind": "oracle",
-                                "sample": f"whole workload, one residual + one HVP, best of 2 "
-                                          f"({t:.2f} s each)"}
+        cpu = cpu_leg(m, u, v, r.double().cpu().numpy(), y.double().cpu().numpy(), r64.cpu().numpy(),
+                      y64.cpu().numpy(), float(e32[0]), float(e64[0]))
+        line["cpu_baseline"] = cpu.pop("cpu_baseline")
+        precision.update(cpu)
+    line["precision_error"] = precision
     if rank == 0:
         print(json.dumps(line))
+
+
+def cpu_info():
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return model, os.cpu_count()
+
+
+def cpu_leg(m, u, v, r32, y32, r64, y64, e32, e64):
+    """The FP64 CPU oracle (single thread, pinned to one core) on the whole
+    workload: one residual + one HVP at the FP64 state, timed, and the same at
+    the FP32-rounded state; their outputs give the FP32 and FP64 GPU paths'
+    errors against the oracle (precision pattern (1))."""
+    import numpy as np
+    import oracle
+    om = oracle.OracleMesh.from_mesh(m)
+    model, ncpu = cpu_info()
+    try:
+        old = os.sched_getaffinity(0)
+        core = min(old)
+        os.sched_setaffinity(0, {core})
+        pinned = f"core {core} (sched_setaffinity, as taskset -c {core})"
+    except (AttributeError, OSError):
+        old, pinned = None, "not pinned"
+    try:
+        ts = []
+        t0 = time.perf_counter()
+        ro = om.residual(u)
+        yo = om.hvp(u, v)
+        ts.append(time.perf_counter() - t0)
+        u32 = u.astype(np.float32).astype(np.float64)
+        v32 = v.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        ro32 = om.residual(u32)
+        yo32 = om.hvp(u32, v32)
+        ts.append(time.perf_counter() - t0)
+        psi = om.energy(u)
+        psi32 = om.energy(u32)
+    finally:
+        if old is not None:
+            os.sched_setaffinity(0, old)
+    t = min(ts)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    out = {"cpu_baseline": {"value": m.n_el / t / 1e9, "unit": "GElem/s", "cores": 1, "kind": "oracle",
+                            "sample": f"whole workload, one residual + one HVP, best of 2 ({t:.2f} s each; "
+                                      "at the FP64 state and at its FP32 rounding)",
+                            "cpu_model": model, "nproc": ncpu, "pinned": pinned},
+           "residual_f32_vs_oracle": rel(r32, ro), "hvp_f32_vs_oracle": rel(y32, yo),
+           "energy_f32_vs_oracle": abs(e32 - psi) / abs(psi),
+           "residual_f32_vs_oracle_at_f32_inputs": rel(r32, ro32), "hvp_f32_vs_oracle_at_f32_inputs": rel(y32, yo32),
+           "energy_f32_vs_oracle_at_f32_inputs": abs(e32 - psi32) / abs(psi32),
+           "input_rounding_alone": {"residual": rel(ro32, ro), "hvp": rel(yo32, yo),
+                                    "what": "oracle at the FP32-rounded state against the oracle at the FP64 state"},
+           "residual_f64_vs_oracle": rel(r64, ro), "hvp_f64_vs_oracle": rel(y64, yo),
+           "energy_f64_vs_oracle": abs(e64 - psi) / abs(psi)}
+    return out
 
 
 def main():
