@@ -100,3 +100,77 @@ def test_partition_rejects_more_ranks_than_elements():
     with pytest.raises(ValueError):
         sh.partition(m, m.n_el + 1)
     assert len(sh.partition(m, m.n_el)) == m.n_el
+
+
+class _OracleRankOps(sh.RankOps):
+    """A rank's element work by the oracle on its submesh (no masks: the
+    sharded solver masks after the halo sum)."""
+
+    def __init__(self, sub):
+        import oracle
+        self.om = oracle.OracleMesh(sub.elem_type, sub.coords, sub.conn, sub.mu_e(), sub.lam_e(), None)
+        self.d = sub.dim
+
+    def residual(self, u):
+        return torch.as_tensor(self.om.residual(u.numpy(), mask_out=False))
+
+    def hvp(self, u, v):
+        return torch.as_tensor(self.om.hvp(u.numpy(), v.numpy(), mask_in=False, mask_out=False))
+
+    def energy(self, u):
+        psi, S, st = self.om.energy_status(u.numpy())
+        return (0.0 if st == 3 else psi), S, (1.0 if st == 3 else 0.0)
+
+    def block_diag(self, u):
+        return torch.as_tensor(self.om.block_diag(u.numpy()))
+
+
+import torch  # noqa: E402  (the worker processes import it themselves)
+
+
+def _solve_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    m = mg.workload_tet(4, seed=1, random_moduli=1)
+    s = sh.partition(m, world)[rank]
+    sub = sh.submesh(m, s)
+    mask = torch.as_tensor(sub.dirichlet.ravel().astype(bool))
+    ubar = torch.as_tensor(sub.ubar.ravel())
+    u = torch.zeros(s.n_local * m.dim, dtype=torch.float64)
+    st = sh.sharded_load_step(_OracleRankOps(sub), s, mask, ubar, 0.0, 0.05, u)
+    st2 = sh.sharded_load_step(_OracleRankOps(sub), s, mask, ubar, 0.05, 0.1, u)
+    out[rank] = (s.nodes, u.numpy().copy(), st, st2)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_load_steps_match_the_single_rank_solve(world):
+    """Two Newton-CG load steps on gloo ranks, the oracle as each rank's
+    element work, residuals / HVPs / nodal blocks through halo_sum and every
+    dot product and norm through dot: the displacements equal the single-rank
+    oracle load steps to 1e-10 and are bitwise the same on every rank that
+    holds a node; every rank takes the same iteration counts."""
+    import oracle
+    out = mp.Manager().dict()
+    mp.spawn(_solve_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    m = mg.workload_tet(4, seed=1, random_moduli=1)
+    om = oracle.OracleMesh.from_mesh(m)
+    uo = np.zeros(m.n_nodes * 3)
+    assert om.load_step(m.ubar.ravel(), 0.0, 0.05, uo).status == 0
+    assert om.load_step(m.ubar.ravel(), 0.05, 0.1, uo).status == 0
+    d = m.dim
+    seen, stats = {}, set()
+    for rank in range(world):
+        nodes, u, st, st2 = out[rank]
+        assert st["status"] == 0 and st2["status"] == 0
+        stats.add((st["newton_iters"], st["cg_iters"], st2["newton_iters"], st2["cg_iters"]))
+        idx = (nodes[:, None] * d + np.arange(d)).ravel()
+        assert np.linalg.norm(u - uo[idx]) <= 1e-10 * np.linalg.norm(uo[idx])
+        for k, n in enumerate(nodes):
+            key = int(n)
+            vals = u[k * d:(k + 1) * d].tobytes()
+            assert seen.setdefault(key, vals) == vals
+    assert len(stats) == 1  # the same decisions on every rank
+    assert len(seen) == m.n_nodes
