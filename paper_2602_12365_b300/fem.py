@@ -308,18 +308,22 @@ class Mesh:
             L.check(rc)
         return st.as_dict()
 
-    def tangent_solve(self, u, b, rtol=1e-8, cg_dtype=torch.float64, cg_max=0, stream=None):
+    def tangent_solve(self, u, b, rtol=1e-8, cg_dtype=torch.float64, cg_max=0, stream=None, check=True):
         """x with M K(u) M x = M b (block-Jacobi PCG, fem_tangent_solve);
-        returns (x, iterations)."""
+        returns (x, iterations), or (x, iterations, status) with
+        ``check=False`` (x is the last iterate when the cap is reached)."""
         if u.dtype != torch.float64 or b.dtype != torch.float64:
             raise TypeError("u and b must be float64")
         self._check_vec(u, b)
         x = torch.empty_like(u)
         it = C.c_int64(0)
-        L.check(L.lib().fem_tangent_solve(self._h, L.FEM_F64 if cg_dtype == torch.float64 else L.FEM_F32,
-                                          _ptr(u), _ptr(b), _ptr(x), float(rtol), int(cg_max),
-                                          C.byref(it), _stream(stream)))
-        return x, it.value
+        rc = L.lib().fem_tangent_solve(self._h, L.FEM_F64 if cg_dtype == torch.float64 else L.FEM_F32,
+                                       _ptr(u), _ptr(b), _ptr(x), float(rtol), int(cg_max),
+                                       C.byref(it), _stream(stream))
+        if check:
+            L.check(rc)
+            return x, it.value
+        return x, it.value, rc
 
     def set_moduli(self, mu, lam, stream=None):
         """Replace the per-element moduli (host arrays, element order)."""
