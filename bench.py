@@ -82,8 +82,8 @@ def measured_peaks():
 # the sources that define what a residual or HVP call runs (tile and
 # finalize kernels, plan, records, launch); the solver, learned-
 # preconditioner, sparse and ablation sources do not change those kernels
-KERNEL_SOURCES = ("fem_api.cu", "fem_internal.h", "fem_kernels.cuh", "fem_material.cuh", "fem_plan.cpp",
-                  "fem_plan.h", "fem_vec.cuh")
+KERNEL_SOURCES = ("fem_api.cu", "fem_internal.h", "fem_kernels.cuh", "fem_material.cuh", "fem_pair.cuh",
+                  "fem_plan.cpp", "fem_plan.h", "fem_vec.cuh")
 
 
 SPMV_SOURCES = ("fem_spmv.cu",)
@@ -435,7 +435,7 @@ def hex_arm(dev, flush_l2, steps, hex_steps):
                          "peak_how": "measured: fem_fp32_fma_rate (8 independent FMA chains per thread, 8 blocks "
                                      "of 256 per SM, best of 5); nominal: SMs x 128 FP32 lanes x 2 x 2.032 GHz"},
             "l2": "flushed before every call",
-            "newton_mixed": {"s_per_load_step": statistics.median(times), "s_each": times,
+            "newton_mixed": {"s_per_load_step": statistics.median(times) if times else None, "s_each": times,
                              "newton_iters": newton, "cg_iters": cg,
                              "what": "mixed precision (FP32 CG with FP64 dots, FP64 residual and energy), block "
                                      "Jacobi, relative residual 1e-8, top shear 0.1 in 10 load steps"}}

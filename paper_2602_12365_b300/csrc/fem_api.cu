@@ -318,8 +318,12 @@ KFn pick_ncm(int op) {
     }
 }
 
-KFn pair_kernel_for(int et, int op) {
+KFn pair_kernel_for(int et, int op, bool lin) {
+    if (op == fem::OP_HVP && lin)
+        return et == 0 ? fem::pair_kernel<0, fem::OP_HVP, true> : fem::pair_kernel<1, fem::OP_HVP, true>;
     if (op == fem::OP_HVP) return et == 0 ? fem::pair_kernel<0, fem::OP_HVP> : fem::pair_kernel<1, fem::OP_HVP>;
+    if (op == fem::OP_LINEARIZE)
+        return et == 0 ? fem::pair_kernel<0, fem::OP_LINEARIZE> : fem::pair_kernel<1, fem::OP_LINEARIZE>;
     return et == 0 ? fem::pair_kernel<0, fem::OP_RESIDUAL> : fem::pair_kernel<1, fem::OP_RESIDUAL>;
 }
 
@@ -508,12 +512,24 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     // asks for it (Neo-Hookean; per element for P1, per Gauss point for Q1)
     const bool lin = op == fem::OP_HVP && (flags & femi::kFlagUseLin) && !ncm;
     flags &= ~femi::kFlagUseLin;
+    // FP32 P1 (Neo-Hookean, the handle's own workspace): the pair kernels for
+    // the residual, the HVP (at u, or from the stored linearisation, which
+    // the pair linearisation pass writes in pair-record order) and the
+    // linearisation itself; an HVP with the last-CTA vKv total stays on the
+    // tile kernel
+    const bool pair_ok = FEM_PAIR_KERNELS && dtype == FEM_F32 && m->prec != nullptr && !ncm && scratch == nullptr;
+    const bool pair = pair_ok && (op == fem::OP_RESIDUAL || op == fem::OP_LINEARIZE ||
+                                  (op == fem::OP_HVP && out_scalar == nullptr));
+    if (lin && pair_ok && !pair)
+        return fail(FEM_ERR_ARG, "the FP32 stored linearisation serves HVPs without a vKv total");
     if (op == fem::OP_LINEARIZE) {
         if (m->ncm) return fail(FEM_ERR_ARG, "the stored linearisation covers the Neo-Hookean law");
         if (!m->lin[pi]) {
             void* q = nullptr;
             const size_t per_elem = m->etype == 2 ? 8 * fem::kHexLinVals : fem::kLinVals;
-            fem_status s = zalloc(m, &q, (size_t)m->plan.n_rounds() * 32 * per_elem * tsize, st);
+            size_t bytes = (size_t)m->plan.n_rounds() * 32 * per_elem * tsize;
+            if (pair_ok) bytes = std::max(bytes, (size_t)m->n_pairs * fem::kPairLinBytes);
+            fem_status s = zalloc(m, &q, bytes, st);
             if (s != FEM_OK) return s;
             m->lin[pi] = q;
         }
@@ -561,17 +577,13 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
     p.out_mu = out_mu;
     p.out_lam = out_lam;
     p.flags = flags;
-    // FP32 P1 residual and HVP (Neo-Hookean, no vKv, own workspace): the pair
-    // kernels, two elements per lane in paired FP32 arithmetic
-    const bool pair = FEM_PAIR_KERNELS && dtype == FEM_F32 && m->prec != nullptr && !ncm && !lin &&
-                      scratch == nullptr &&
-                      (op == fem::OP_RESIDUAL || (op == fem::OP_HVP && out_scalar == nullptr && vkv_tiles == 0));
     p.prec = m->prec;
     p.prec_bytes = m->prec_bytes;
     p.tile_pair_ptr = m->tile_pair_ptr;
-    const int smem = pair ? fem::pair_layout(m->etype, op, m->max_nlp, m->prec_bytes).total
-                          : fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi], lin).total;
-    KFn fn = pair ? pair_kernel_for(m->etype, op) : kernel_for(m->etype, dtype, op, ncm, lin);
+    const int smem =
+        pair ? fem::pair_layout(m->etype, op, lin, m->max_nlp, fem::pair_copy_bytes(m->etype, m->per_elem_mat, lin)).total
+             : fem::smem_layout(m->etype, tsize, op, m->max_nlp, (int)m->rec_bytes[pi], lin).total;
+    KFn fn = pair ? pair_kernel_for(m->etype, op, lin) : kernel_for(m->etype, dtype, op, ncm, lin);
     int grid = 0;
     {
         // raise the dynamic shared-memory limit once per (device, kernel)
@@ -864,6 +876,7 @@ fem_status fem_mesh_create(const fem_mesh_desc* d, fem_mesh** out, void* stream)
         std::vector<int32_t> tpp;
         pack_pair_records(m, d, precs, tpp, m->max_nlp);
         m->prec_bytes = fem::pair_rec_bytes(m->etype, m->per_elem_mat);
+        m->n_pairs = tpp.back();
         if ((s = upload(m, &m->prec, precs.data(), precs.size(), st)) != FEM_OK) goto fail_out;
         if ((s = upload(m, &m->tile_pair_ptr, tpp.data(), tpp.size(), st)) != FEM_OK) goto fail_out;
         if (cudaStreamSynchronize(st) != cudaSuccess) {

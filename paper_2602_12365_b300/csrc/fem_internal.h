@@ -71,6 +71,7 @@ struct fem_mesh {
     // (pair, lane, half) slot (-1 empty) for moduli updates
     uint8_t* prec = nullptr;
     int prec_bytes = 0;
+    int64_t n_pairs = 0;
     int32_t* tile_pair_ptr = nullptr;
     std::vector<int32_t> pair_elem;
 };

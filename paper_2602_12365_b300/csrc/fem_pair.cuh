@@ -29,6 +29,15 @@
 // The scatter adds A's contributions (low halves) for all lanes, then B's
 // (high halves): the lanes of one round share no node, and the warp
 // synchronises between the two rounds.
+//
+// Four kernels share the body: the residual and the HVP at (u, v); the
+// linearisation pass (OP_LINEARIZE: per element F^-T, w mu, w (mu - lambda
+// ln J), w lambda at u, written as (A, B) pairs in pair-record order: 12
+// pairs per lane in 6 lane-major 16-byte chunks); and the HVP from that
+// stored linearisation (LIN: no u, no F, F^-1 or ln J; the lin block of a
+// pair travels in the same ring stage as its record), which is the PCG's
+// operator.  The HVPs can leave per-tile FP32-pair partials of v^T K v
+// (vkv_tiles) for the PCG's fused dot product.
 #pragma once
 #include "fem_kernels.cuh"
 
@@ -61,33 +70,49 @@ __host__ __device__ constexpr int pair_rec_bytes(int et, bool mat) {
     return 32 * 16 * (1 + (et == 0 ? 3 : 5) + (mat ? 1 : 0));
 }
 
+// lin block of one pair record: 12 values x 2 elements x 32 lanes
+constexpr int kPairLinBytes = 32 * 16 * 6;
+
+// bytes of the pair record a kernel copies: the geometry prefix (ids and
+// geometry), plus the moduli chunk unless the kernel reads the stored
+// linearisation (which carries the moduli)
+__host__ __device__ constexpr int pair_copy_bytes(int et, bool mat, bool lin) {
+    return lin ? pair_rec_bytes(et, false) : pair_rec_bytes(et, mat);
+}
+
 struct PairLayout {
-    int off_v, buf_bytes, off_buf0, off_buf1, off_acc, acc_stride, off_red, off_tab, off_tabp, off_ring, off_bar, total;
+    int off_u, off_v, buf_bytes, off_buf0, off_buf1, off_acc, acc_stride, off_red, off_tab, off_tabp, off_ring,
+        stage_bytes, off_bar, total;
 };
 
-// node buffers hold max_nlp + 1 entries (the last is the dummy node)
-__host__ __device__ inline PairLayout pair_layout(int et, int op, int max_nlp, int prec_bytes) {
+// node buffers hold max_nlp + 1 entries (the last is the dummy node); u
+// unless LIN, v for the HVPs, accumulators unless OP_LINEARIZE
+__host__ __device__ inline PairLayout pair_layout(int et, int op, bool lin, int max_nlp, int copy_bytes) {
     const int vw = et == 0 ? 2 : 4;
     const int nodes = max_nlp + 1;
+    const int vec = align16(nodes * vw * 4);
+    const bool has_u = !lin, has_v = op == OP_HVP, has_acc = op != OP_LINEARIZE;
     PairLayout L;
-    L.off_v = align16(nodes * vw * 4);
-    L.buf_bytes = align16(op == OP_HVP ? 2 * L.off_v : L.off_v);
+    L.off_u = 0;
+    L.off_v = has_u ? vec : 0;
+    L.buf_bytes = (has_u ? vec : 0) + (has_v ? vec : 0);
     L.off_buf0 = 0;
     L.off_buf1 = L.buf_bytes;
     int o = 2 * L.buf_bytes;
     // per-warp accumulator copies at a 16-byte stride (acc_stride floats),
     // so that every copy starts on a 16-byte boundary for vector stores
     L.off_acc = o;
-    L.acc_stride = align16(nodes * vw * 4) / 4;
+    L.acc_stride = has_acc ? vec / 4 : 0;
     o += kWarps * L.acc_stride * 4;
-    L.off_red = o;  // the CTA's status flags
-    o = align16(o + 16);
+    L.off_red = o;  // the CTA's status flags, then the warps' v^T K v pairs
+    o = align16(o + 16 + kWarps * 8);
     L.off_tab = o;
     o = align16(o + kMaxTilesPerCta * 16);
     L.off_tabp = o;
     o = align16(o + kMaxTilesPerCta * 4);
+    L.stage_bytes = copy_bytes + (lin ? kPairLinBytes : 0);
     L.off_ring = o = align16(o);
-    o += kWarps * prec_bytes;
+    o += kWarps * L.stage_bytes;
     L.off_bar = o = align16(o);
     o += kWarps * 8;
     L.total = align16(o);
@@ -100,32 +125,38 @@ __device__ __forceinline__ F2 pair_of(const float4 (&gc)[5], int j) {
     return (j & 1) ? mk2(c.z, c.w) : mk2(c.x, c.y);
 }
 
-template <int ET, int OP>
+template <int ET, int OP, bool LIN>
 __device__ __forceinline__ void pair_body(const KParams& p) {
     using PT = PairT<ET>;
     constexpr int D = PT::D, NEN = PT::NEN, NM1 = NEN - 1, NG = PT::NG, NCH = PT::NCH;
     constexpr int VW = D == 2 ? 2 : 4;
+    constexpr bool kLinz = OP == OP_LINEARIZE;     // writes the linearisation
     constexpr bool kHvp = OP == OP_HVP;
-    static_assert(OP == OP_RESIDUAL || OP == OP_HVP, "pair kernels: residual and HVP");
+    constexpr bool kNeedU = !LIN, kNeedV = kHvp, kAcc = !kLinz;
+    static_assert(OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_LINEARIZE, "pair kernels: residual, HVP, linearise");
+    static_assert(!LIN || kHvp, "the stored linearisation serves the HVP");
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int G = gridDim.x, cta = blockIdx.x;
     const int n_my = (p.n_tiles > cta) ? (p.n_tiles - cta + G - 1) / G : 0;
     if (n_my == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const PairLayout L = pair_layout(ET, OP, p.max_nlp, p.prec_bytes);
+    const int copy_bytes = pair_copy_bytes(ET, p.has_mat != 0, LIN);
+    const PairLayout L = pair_layout(ET, OP, LIN, p.max_nlp, copy_bytes);
     const int nodes = p.max_nlp + 1;
     float* sAcc = reinterpret_cast<float*>(smem + L.off_acc);
     int* sFlag = reinterpret_cast<int*>(smem + L.off_red);
+    float* sRed = reinterpret_cast<float*>(smem + L.off_red + 16);  // per warp (hi, lo) of v^T K v
     int4* tab = reinterpret_cast<int4*>(smem + L.off_tab);  // (node begin, padded count, round begin, rounds)
     int* tabp = reinterpret_cast<int*>(smem + L.off_tabp);  // first pair record of the tile
-    uint8_t* ring = smem + L.off_ring + warp * p.prec_bytes;
+    uint8_t* ring = smem + L.off_ring + warp * L.stage_bytes;
     uint64_t* rbar = reinterpret_cast<uint64_t*>(smem + L.off_bar) + warp;
-    auto bufU = [&](int b) { return reinterpret_cast<float*>(smem + (b ? L.off_buf1 : L.off_buf0)); };
+    auto bufU = [&](int b) { return reinterpret_cast<float*>(smem + (b ? L.off_buf1 : L.off_buf0) + L.off_u); };
     auto bufV = [&](int b) { return reinterpret_cast<float*>(smem + (b ? L.off_buf1 : L.off_buf0) + L.off_v); };
     const float* gu = static_cast<const float*>(p.u);
     const float* gv = static_cast<const float*>(p.v);
     const float mu0 = (float)p.mu0, lam0 = (float)p.lam0;
+    const bool want_vkv = kHvp && p.vkv_tiles != 0;
     int flags_local = 0;
 
     // 0. tile table, barriers, the dummy node (zero in both buffers)
@@ -143,8 +174,8 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
     }
     if (tid < 2 * VW) {
         const int b = tid / VW, c = tid % VW;
-        bufU(b)[(nodes - 1) * VW + c] = 0.f;
-        if constexpr (kHvp) bufV(b)[(nodes - 1) * VW + c] = 0.f;
+        if constexpr (kNeedU) bufU(b)[(nodes - 1) * VW + c] = 0.f;
+        if constexpr (kNeedV) bufV(b)[(nodes - 1) * VW + c] = 0.f;
     }
     __syncthreads();
 
@@ -165,8 +196,10 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             M.s[k] = -1;
             if (j < tb.y) {
                 M.g[k] = __ldg(p.node_gid + tb.x + j);
-                M.s[k] = __ldg(p.node_slot + tb.x + j);
-                M.m |= (uint32_t)__ldg(p.node_mask_local + tb.x + j) << (8 * k);
+                if constexpr (kAcc) {
+                    M.s[k] = __ldg(p.node_slot + tb.x + j);
+                    M.m |= (uint32_t)__ldg(p.node_mask_local + tb.x + j) << (8 * k);
+                }
             }
         }
     };
@@ -179,8 +212,8 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             if (g < 0) return;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                cp_async<4>(bu + j * VW + c, gu + g * D + c);
-                if constexpr (kHvp) cp_async<4>(bv + j * VW + c, gv + g * D + c);
+                if constexpr (kNeedU) cp_async<4>(bu + j * VW + c, gu + g * D + c);
+                if constexpr (kNeedV) cp_async<4>(bv + j * VW + c, gv + g * D + c);
             }
         };
 #pragma unroll
@@ -189,18 +222,15 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
         for (int j = tid + kThreads * kMeta; j < tb.y; j += kThreads) one(j, __ldg(p.node_gid + tb.x + j));
         cp_async_commit();
     };
-    // this warp's pair records of tile i: warp w runs the rounds
-    // [r0 + w q + min(w, R % kWarps), ...), n_w = q + (w < R % kWarps), q = R / kWarps,
-    // as ceil(n_w / 2) pairs; the tile's pairs are stored warp by warp
+    // this warp's pair records of tile i
     auto my_pairs = [&](int i, int& p0, int& np) {
         const int R = tab[i].w;
         p0 = tabp[i] + pair_first(R, warp);
         np = pair_count(R, warp);
     };
-    // ring producer (lane 0): one pair record per stage, across tiles
     // ring producer (lane 0): a cursor over the warp's pair records across
     // its tiles gives the next record index (-1 past the last); one record
-    // per copy, one stage per warp
+    // (and, for LIN, its lin block) per copy, one stage per warp
     struct Cursor {
         int i, it, p0, np;
     };
@@ -215,10 +245,15 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
     Cursor cc{0, 0, 0, 0};
     my_pairs(0, cc.p0, cc.np);
     int issued = 0;
+    const unsigned char* glin = static_cast<const unsigned char*>(p.lin);
     auto issue_next = [&]() {
         const int64_t r = next_rec(cc);
         if (r < 0) return;
-        bulk_load(ring, p.prec + r * p.prec_bytes, (uint32_t)p.prec_bytes, rbar);
+        if constexpr (LIN)  // the record's geometry prefix, then its lin block; read once: evict first
+            bulk_load2_hint(ring, p.prec + r * p.prec_bytes, (uint32_t)copy_bytes, ring + copy_bytes,
+                            glin + r * kPairLinBytes, (uint32_t)kPairLinBytes, rbar, l2_evict_first());
+        else
+            bulk_load(ring, p.prec + r * p.prec_bytes, (uint32_t)copy_bytes, rbar);
         ++issued;
     };
 
@@ -236,6 +271,7 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
     bool timed_out = false;
     int inv = 0;
     for (int i = 0; i < n_my; ++i) {
+        const int t = cta + i * G;
         float* sU = bufU(i & 1);
         float* sV = bufV(i & 1);
         const int nlp = tab[i].y;
@@ -249,8 +285,8 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                fin = fin && finite_(sU[j * VW + c]);
-                if constexpr (kHvp) {
+                if constexpr (kNeedU) fin = fin && finite_(sU[j * VW + c]);
+                if constexpr (kNeedV) {
                     if ((p.flags & 2u) && ((m >> c) & 1)) sV[j * VW + c] = 0.f;
                     fin = fin && finite_(sV[j * VW + c]);
                 }
@@ -262,7 +298,7 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             if (tid + kThreads * k < nlp) fixup(tid + kThreads * k, cur.g[k], (cur.m >> (8 * k)) & 0xffu);
         for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
             fixup(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_mask_local + nbase + j));
-        {
+        if constexpr (kAcc) {
             float* myz = sAcc + (size_t)warp * L.acc_stride;
             float4* z = reinterpret_cast<float4*>(myz);
             const int nz = (nlp * VW + 3) / 4;
@@ -275,6 +311,7 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
         my_pairs(i, p0, np);
         float* myAcc = sAcc + (size_t)warp * L.acc_stride;
         bool gathered = (i + 1 >= n_my);
+        float vk_hi = 0.f, vk_lo = 0.f;  // this lane's v^T K v over the tile (TwoSum pair)
         for (int k = 0; k < np && !timed_out; ++k) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(rbar, (uint32_t)(consumed & 1)))) {
                 timed_out = true;  // warp-uniform
@@ -288,8 +325,13 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             for (int c = 0; c < NCH; ++c) gc[c] = reinterpret_cast<const float4*>(st + 512 * (1 + c))[lane];
 #pragma unroll
             for (int c = NCH; c < 5; ++c) gc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 mc = p.has_mat ? reinterpret_cast<const float4*>(st + 512 * (1 + NCH))[lane]
-                                        : make_float4(mu0, mu0, lam0, lam0);
+            float4 mc = make_float4(mu0, mu0, lam0, lam0);
+            if (!LIN && p.has_mat) mc = reinterpret_cast<const float4*>(st + 512 * (1 + NCH))[lane];
+            float4 lc[LIN ? 6 : 1];
+            if constexpr (LIN) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) lc[c] = reinterpret_cast<const float4*>(st + copy_bytes + 512 * c)[lane];
+            }
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_smem();
@@ -309,95 +351,183 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             }
             // gather and differences against the reference (last) node: the
             // scalar differences land in the two halves of the pairs
-            F2 du[NM1][D], dv[NM1][D];
-            {
+            auto diffs = [&](const float* buf, F2 (&dd)[NM1][D]) {
                 float ta[NEN][4], tb[NEN][4];
 #pragma unroll
                 for (int a = 0; a < NEN; ++a) {
-                    lds_vec<VW, float>(sU, ia[a], ta[a]);
-                    lds_vec<VW, float>(sU, ib[a], tb[a]);
+                    lds_vec<VW, float>(buf, ia[a], ta[a]);
+                    lds_vec<VW, float>(buf, ib[a], tb[a]);
                 }
 #pragma unroll
                 for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                    for (int c = 0; c < D; ++c) du[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
-                if constexpr (kHvp) {
-#pragma unroll
-                    for (int a = 0; a < NEN; ++a) {
-                        lds_vec<VW, float>(sV, ia[a], ta[a]);
-                        lds_vec<VW, float>(sV, ib[a], tb[a]);
-                    }
-#pragma unroll
-                    for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                        for (int c = 0; c < D; ++c) dv[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
-                }
-            }
+                    for (int c = 0; c < D; ++c) dd[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
+            };
             F2 g[NM1][D];
 #pragma unroll
             for (int a = 0; a < NM1; ++a)
 #pragma unroll
                 for (int c = 0; c < D; ++c) g[a][c] = pair_of(gc, a * D + c);
-            F2 wdJ = pair_of(gc, NG - 1);
-            F2 H[D][D];
-            outer_sum<D, F2>(du, g, NM1, H);
-            Kin<D, F2> kin;
-            kinematics<D, F2, true>(H, kin);
-            const int bad = 3 & ~kin.ok;  // empty halves have H = 0, J = 1
-            inv |= bad;
-            wdJ = vsel(kin.ok, wdJ, 0.f);  // inverted halves contribute nothing
-            const F2 wmu = wdJ * mk2(mc.x, mc.y), wlam = wdJ * mk2(mc.z, mc.w);
             F2 P[D][D];
-            if constexpr (kHvp) {
-                F2 dF[D][D];
+            F2 dF[D][D];
+            if constexpr (kNeedV) {
+                F2 dv[NM1][D];
+                diffs(sV, dv);
                 outer_sum<D, F2>(dv, g, NM1, dF);
-                tangent<D, F2>(dF, kin, wmu, wlam, P);
-            } else {
-                stress<D, F2>(H, kin, wmu, wlam, P);
             }
-            F2 f[NEN][D];
+            if constexpr (LIN) {
+                // dP = w mu dF + w (mu - lambda ln J) F^-T dF^T F^-T + w lambda tr(F^-1 dF) F^-T
+                // from the stored F^-T and scaled moduli (zero for empty or inverted elements)
+                auto lp = [&](int j) {
+                    const float4 c = lc[j >> 1];
+                    return (j & 1) ? mk2(c.z, c.w) : mk2(c.x, c.y);
+                };
+                F2 FiT[D][D];
 #pragma unroll
-            for (int a = 0; a < NM1; ++a)
+                for (int i2 = 0; i2 < D; ++i2)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) FiT[i2][j] = lp(i2 * D + j);
+                const F2 wmu = lp(9), c1 = lp(10), wlam = lp(11);
+                F2 trA = FiT[0][0] * dF[0][0];
+#pragma unroll
+                for (int i2 = 0; i2 < D; ++i2)
+#pragma unroll
+                    for (int j = 0; j < D; ++j)
+                        if (i2 + j > 0) trA = vfma(FiT[i2][j], dF[i2][j], trA);
+                F2 M[D][D];  // dF^T F^-T
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        F2 t2 = dF[0][a] * FiT[0][j];
+#pragma unroll
+                        for (int l = 1; l < D; ++l) t2 = vfma(dF[l][a], FiT[l][j], t2);
+                        M[a][j] = t2;
+                    }
+                const F2 c2 = wlam * trA;
+#pragma unroll
+                for (int i2 = 0; i2 < D; ++i2)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        F2 B = FiT[i2][0] * M[0][j];
+#pragma unroll
+                        for (int a = 1; a < D; ++a) B = vfma(FiT[i2][a], M[a][j], B);
+                        P[i2][j] = vfma(c2, FiT[i2][j], vfma(c1, B, wmu * dF[i2][j]));
+                    }
+            } else {
+                F2 du[NM1][D];
+                diffs(sU, du);
+                F2 wdJ = pair_of(gc, NG - 1);
+                F2 H[D][D];
+                outer_sum<D, F2>(du, g, NM1, H);
+                Kin<D, F2> kin;
+                kinematics<D, F2, true>(H, kin);
+                const int bad = 3 & ~kin.ok;  // empty halves have H = 0, J = 1
+                inv |= bad;
+                wdJ = vsel(kin.ok, wdJ, 0.f);  // inverted halves contribute nothing
+                const F2 mu = mk2(mc.x, mc.y), lam = mk2(mc.z, mc.w);
+                const F2 wmu = wdJ * mu, wlam = wdJ * lam;
+                if constexpr (kLinz) {
+                    // F^-T, w mu, w (mu - lambda ln J), w lambda: 12 pairs in 6
+                    // lane-major chunks of the pair's lin block (2D uses the
+                    // first four F^-T slots)
+                    F2 o[12];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) o[q] = mk2(0.f, 0.f);
+#pragma unroll
+                    for (int i2 = 0; i2 < D; ++i2)
+#pragma unroll
+                        for (int j = 0; j < D; ++j)
+                            o[i2 * D + j] = (i2 == j) ? kin.G[i2][j] + mk2(1.f, 1.f) : kin.G[i2][j];
+                    o[9] = wmu;
+                    o[10] = wdJ * (mu - lam * kin.lnJ);
+                    o[11] = wlam;
+                    float4* dst = reinterpret_cast<float4*>(static_cast<unsigned char*>(p.lin) +
+                                                            (int64_t)(p0 + k) * kPairLinBytes) + lane;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        dst[32 * c] = make_float4(o[2 * c].v.x, o[2 * c].v.y, o[2 * c + 1].v.x, o[2 * c + 1].v.y);
+                } else if constexpr (kHvp) {
+                    tangent<D, F2>(dF, kin, wmu, wlam, P);
+                } else {
+                    stress<D, F2>(H, kin, wmu, wlam, P);
+                }
+            }
+            if constexpr (kAcc) {
+                if constexpr (kHvp) {
+                    if (want_vkv) {  // w dP : dF of both halves
+                        F2 e = P[0][0] * dF[0][0];
+#pragma unroll
+                        for (int i2 = 0; i2 < D; ++i2)
+#pragma unroll
+                            for (int j = 0; j < D; ++j)
+                                if (i2 + j > 0) e = vfma(P[i2][j], dF[i2][j], e);
+                        ff_add(vk_hi, vk_lo, e.v.x);
+                        ff_add(vk_hi, vk_lo, e.v.y);
+                    }
+                }
+                F2 f[NEN][D];
+#pragma unroll
+                for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        F2 s2 = P[c][0] * g[a][0];
+#pragma unroll
+                        for (int j = 1; j < D; ++j) s2 = vfma(P[c][j], g[a][j], s2);
+                        f[a][c] = s2;
+                    }
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    F2 s = P[c][0] * g[a][0];
+                    F2 s2 = -f[0][c];
 #pragma unroll
-                    for (int j = 1; j < D; ++j) s = vfma(P[c][j], g[a][j], s);
-                    f[a][c] = s;
+                    for (int a = 1; a < NM1; ++a) s2 = s2 - f[a][c];
+                    f[NM1][c] = s2;
                 }
+                // scatter round A (low halves), then round B (high halves).  The
+                // lanes of one round hit distinct nodes of the warp's own copy, so
+                // the adds of a node come in round order (fixed, reproducible)
+                auto scatter = [&](const int (&id)[NEN], int h) {
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                F2 s = -f[0][c];
+                    for (int a = 0; a < NEN; ++a) {
+                        float cur4[4];
+                        lds_vec<VW, float>(myAcc, id[a], cur4);
 #pragma unroll
-                for (int a = 1; a < NM1; ++a) s = s - f[a][c];
-                f[NM1][c] = s;
-            }
-            // scatter round A (low halves), then round B (high halves).  The
-            // lanes of one round hit distinct nodes of the warp's own copy, so
-            // the adds of a node come in round order (fixed, reproducible)
-            auto scatter = [&](const int (&id)[NEN], int h) {
-#pragma unroll
-                for (int a = 0; a < NEN; ++a) {
-                    float cur4[4];
-                    lds_vec<VW, float>(myAcc, id[a], cur4);
-#pragma unroll
-                    for (int c = 0; c < D; ++c) cur4[c] += vcomp(f[a][c], h);
-                    // a fresh padding value keeps the store one 16-byte access
-                    if constexpr (VW > D) cur4[VW - 1] = 0.f;
-                    sts_vec<VW, float>(myAcc, id[a], cur4);
-                }
-            };
-            scatter(ia, 0);
-            __syncwarp();
-            scatter(ib, 1);
-            __syncwarp();
+                        for (int c = 0; c < D; ++c) cur4[c] += vcomp(f[a][c], h);
+                        // a fresh padding value keeps the store one 16-byte access
+                        if constexpr (VW > D) cur4[VW - 1] = 0.f;
+                        sts_vec<VW, float>(myAcc, id[a], cur4);
+                    }
+                };
+                scatter(ia, 0);
+                __syncwarp();
+                scatter(ib, 1);
+                __syncwarp();
+            }  // kAcc
         }
         if (!gathered && !timed_out) gather(i + 1, nxt);  // a warp without pairs in this tile
-        __syncthreads();
 
-        // 4. combine the warp copies in warp order; private nodes to the
+        // 4. the tile's v^T K v partial: warps in order, FP32 pairs
+        if (want_vkv) {
+            ff_warp_total(vk_hi, vk_lo);
+            if (lane == 0) {
+                sRed[warp * 2 + 0] = vk_hi;
+                sRed[warp * 2 + 1] = vk_lo;
+            }
+        }
+        __syncthreads();
+        if (want_vkv && tid == 0) {
+            float hi = 0.f, lo = 0.f;
+            for (int w = 0; w < kWarps; ++w) {
+                ff_add(hi, lo, sRed[w * 2 + 0]);
+                lo += sRed[w * 2 + 1];
+            }
+            reinterpret_cast<float*>(p.tile_red + (int64_t)t * 4)[0] = hi;
+            reinterpret_cast<float*>(p.tile_red + (int64_t)t * 4)[1] = lo;
+        }
+
+        // 5. combine the warp copies in warp order; private nodes to the
         // output, shared nodes to their partial slot
-        {
+        if constexpr (kAcc) {
             float* part = static_cast<float*>(p.partial);
             float* out = static_cast<float*>(p.out);
             auto combine = [&](int j, int g, int slot, uint32_t msk) {
@@ -441,9 +571,9 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
 }
 
 // four CTAs of kThreads per SM: at most 128 registers per thread
-template <int ET, int OP>
+template <int ET, int OP, bool LIN = false>
 __global__ void __launch_bounds__(kThreads, 4) pair_kernel(const KParams p) {
-    pair_body<ET, OP>(p);
+    pair_body<ET, OP, LIN>(p);
 }
 
 }  // namespace fem
