@@ -525,6 +525,30 @@ __host__ __device__ constexpr double hex_dN(int a, int q, int j) {
                           (1.0 + hex_sign(a, 1) * hex_xi(q, 1));
 }
 
+// the same gradients as a table in constant memory, for a rolled loop over
+// the Gauss points (all lanes read the same entry: a broadcast)
+template <typename T>
+struct HexDN {
+    T v[8][7][3];  // [point][node 1..7][reference direction]
+};
+template <typename T>
+__host__ __device__ constexpr HexDN<T> make_hex_dn() {
+    HexDN<T> t{};
+    for (int q = 0; q < 8; ++q)
+        for (int a = 0; a < 7; ++a)
+            for (int j = 0; j < 3; ++j) t.v[q][a][j] = (T)hex_dN(a + 1, q, j);
+    return t;
+}
+static __constant__ HexDN<float> c_hex_dn_f = make_hex_dn<float>();
+static __constant__ HexDN<double> c_hex_dn_d = make_hex_dn<double>();
+template <typename T>
+__device__ __forceinline__ T hex_dn(int q, int a, int j) {
+    if constexpr (sizeof(T) == 4)
+        return c_hex_dn_f.v[q][a][j];
+    else
+        return c_hex_dn_d.v[q][a][j];
+}
+
 // ---------------------------------------------------------------------------
 // quadrature-point work, shared by P1 and Q1
 // ---------------------------------------------------------------------------
@@ -1117,18 +1141,23 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
 #pragma unroll
             for (int q = 0; q < kSt - 1; ++q) lin_issue(q);
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        // One Gauss point.  The full HVP runs the points in a rolled loop
+        // with the reference gradients read from constant memory (smaller
+        // code and fewer registers: measured 766 -> 680 us on hex128); the
+        // other operators keep the unrolled loop with compile-time
+        // gradients (measured faster for them)
+        constexpr bool kRoll = OP == OP_HVP && !LIN;
+        auto point = [&](const int q) {
             V gr[NM1][D];
 #pragma unroll
             for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                for (int j = 0; j < D; ++j) gr[a][j] = (V)hex_dN(a + 1, q, j);
+                for (int j = 0; j < D; ++j) gr[a][j] = kRoll ? (V)hex_dn<T>(q, a, j) : (V)hex_dN(a + 1, q, j);
             if constexpr (LIN) {
                 lin_issue(q + kSt - 1);
                 cp_async_wait_group<kSt - 1>();  // point q has landed
                 hex_lin_point<T>(dv, gr, lbuf + ((q % kSt) * kNch * 32 + lane_) * kChunk, valid, scal, acc, fr);
-                continue;
+                return;
             }
             V Jm[D][D];
             outer_sum<D, V>(dx, gr, NM1, Jm);
@@ -1161,7 +1190,7 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
             outer_sum<D, V>(du, g, NM1, H);
             if constexpr (OP == OP_LINEARIZE) {
                 hex_linearize_point<T>(H, Ji, detJ, mu, lam, valid, inv, acc, ninv + q * kNch * 32 * kChunk);
-                continue;
+                return;
             }
             if constexpr (kNeedV) {
                 outer_sum<D, V>(dv, g, NM1, dF);
@@ -1172,6 +1201,13 @@ __device__ __forceinline__ void element_work(const Half<ET, T>* hs, int valid, c
                     for (int j = 0; j < D; ++j) dF[i][j] = splat<V>(S(0));
             }
             qp_work<OP, D, NM1, V>(H, dF, g, detJ, mu, lam, valid, fr, acc, scal, gmu, glam, inv);
+        };
+        if constexpr (kRoll) {
+#pragma unroll 1
+            for (int q = 0; q < 8; ++q) point(q);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) point(q);
         }
         if constexpr (OP == OP_RESIDUAL || OP == OP_HVP) {
 #pragma unroll

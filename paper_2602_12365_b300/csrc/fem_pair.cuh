@@ -208,18 +208,27 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
         const int4 tb = tab[i];
         float* bu = bufU(i & 1);
         float* bv = bufV(i & 1);
-        auto one = [&](int j, int64_t g) {
+        // the HVP's input mask is applied here: a masked component is stored
+        // as zero instead of copied (so nothing rewrites the buffer later)
+        const bool mask_in = kNeedV && (p.flags & 2u);
+        auto one = [&](int j, int64_t g, uint32_t m) {
             if (g < 0) return;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 if constexpr (kNeedU) cp_async<4>(bu + j * VW + c, gu + g * D + c);
-                if constexpr (kNeedV) cp_async<4>(bv + j * VW + c, gv + g * D + c);
+                if constexpr (kNeedV) {
+                    if (mask_in && ((m >> c) & 1))
+                        bv[j * VW + c] = 0.f;
+                    else
+                        cp_async<4>(bv + j * VW + c, gv + g * D + c);
+                }
             }
         };
 #pragma unroll
         for (int k = 0; k < kMeta; ++k)
-            if (tid + kThreads * k < tb.y) one(tid + kThreads * k, M.g[k]);
-        for (int j = tid + kThreads * kMeta; j < tb.y; j += kThreads) one(j, __ldg(p.node_gid + tb.x + j));
+            if (tid + kThreads * k < tb.y) one(tid + kThreads * k, M.g[k], (M.m >> (8 * k)) & 0xffu);
+        for (int j = tid + kThreads * kMeta; j < tb.y; j += kThreads)
+            one(j, __ldg(p.node_gid + tb.x + j), kNeedV ? __ldg(p.node_mask_local + tb.x + j) : 0u);
         cp_async_commit();
     };
     // this warp's pair records of tile i
@@ -276,35 +285,33 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
         float* sV = bufV(i & 1);
         const int nlp = tab[i].y;
         const int64_t nbase = tab[i].x;
+        // this tile's nodes have landed, and every warp is done with the
+        // previous tile's accumulator copies (combined before this barrier)
         cp_async_wait_all();
         __syncthreads();
-        // 2. fix-ups of the gathered values (finite inputs; the HVP's input
-        // mask); zero the accumulators
-        auto fixup = [&](int j, int g, uint32_t m) {
+        // 2. the finite-input check (reads only) and each warp's own
+        // accumulator copy zeroed: no further barrier before the rounds
+        auto fixup = [&](int j, int g) {
             if (g < 0) return;
             bool fin = true;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 if constexpr (kNeedU) fin = fin && finite_(sU[j * VW + c]);
-                if constexpr (kNeedV) {
-                    if ((p.flags & 2u) && ((m >> c) & 1)) sV[j * VW + c] = 0.f;
-                    fin = fin && finite_(sV[j * VW + c]);
-                }
+                if constexpr (kNeedV) fin = fin && finite_(sV[j * VW + c]);
             }
             if (!fin) flags_local |= 2;
         };
 #pragma unroll
         for (int k = 0; k < kMeta; ++k)
-            if (tid + kThreads * k < nlp) fixup(tid + kThreads * k, cur.g[k], (cur.m >> (8 * k)) & 0xffu);
-        for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads)
-            fixup(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_mask_local + nbase + j));
+            if (tid + kThreads * k < nlp) fixup(tid + kThreads * k, cur.g[k]);
+        for (int j = tid + kThreads * kMeta; j < nlp; j += kThreads) fixup(j, __ldg(p.node_gid + nbase + j));
         if constexpr (kAcc) {
             float* myz = sAcc + (size_t)warp * L.acc_stride;
             float4* z = reinterpret_cast<float4*>(myz);
             const int nz = (nlp * VW + 3) / 4;
             for (int j = lane; j < nz; j += 32) z[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncthreads();
+        __syncwarp();
 
         // 3. pairs of rounds
         int p0, np;
@@ -552,7 +559,8 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
                 combine(j, __ldg(p.node_gid + nbase + j), __ldg(p.node_slot + nbase + j),
                         __ldg(p.node_mask_local + nbase + j));
         }
-        __syncthreads();
+        // (the next tile's first barrier also orders these reads of the
+        // copies before their zeroing)
         cur = nxt;
         if (i + 2 < n_my) load_meta(i + 2, nxt);
     }
