@@ -598,7 +598,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
             CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             set_to[key] = smem;
         }
-        // persistent grid: every resident slot, at most kMaxTilesPerCta tiles each
+        // persistent grid: every resident slot, at most max_tiles_per_cta tiles each
         static std::map<std::pair<std::pair<int, const void*>, int>, int> resident;
         auto rk = std::make_pair(key, smem);
         auto ri = resident.find(rk);
@@ -609,7 +609,8 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
             ri = resident.emplace(rk, std::max(1, per_sm) * sms).first;
         }
         grid = std::min(p.n_tiles, ri->second);
-        grid = std::max(grid, (p.n_tiles + fem::kMaxTilesPerCta - 1) / fem::kMaxTilesPerCta);
+        const int cap = pair ? fem::kMaxTilesPerCta : fem::max_tiles_per_cta(m->etype);
+        grid = std::max(grid, (p.n_tiles + cap - 1) / cap);
     }
     {
         // programmatic dependent launch: the CTAs are placed as the previous

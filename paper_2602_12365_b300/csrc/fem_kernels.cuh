@@ -117,6 +117,11 @@ __host__ __device__ constexpr int rounds_per_iter(int et, int tsize, int op, boo
 // scratch, the CTA's tile table, the per-warp record ring and the mbarriers.
 // ---------------------------------------------------------------------------
 constexpr int kMaxTilesPerCta = 16;
+// Q1 tiles are a quarter of the P1 ones (their node buffers are larger) and
+// their kernels hold two CTAs per SM: a cap of 32 keeps the grid at one CTA
+// per resident slot on the 128^3 mesh (8192 tiles) instead of a second,
+// partial wave.
+__host__ __device__ constexpr int max_tiles_per_cta(int et) { return et == 2 ? 2 * kMaxTilesPerCta : kMaxTilesPerCta; }
 
 struct SmemLayout {
     int off_u, off_v, off_x, buf_bytes;  // inside one node buffer
@@ -155,7 +160,7 @@ __host__ __device__ inline SmemLayout smem_layout(int et, int tsize, int op, int
     L.off_red = o;
     o = align16(o + kWarps * 4 * 8 + 16);
     L.off_tab = o;
-    o = align16(o + kMaxTilesPerCta * 16);
+    o = align16(o + max_tiles_per_cta(et) * 16);
     // (Q1 reads its per-point linearisation from global memory, not the ring)
     L.stage_bytes = rounds_per_iter(et, tsize, op, lin) * (rec_bytes + (lin && et != 2 ? 32 * kLinVals * tsize : 0));
     L.off_ring = o = align128(o);

@@ -88,6 +88,100 @@ int colour_tile(const std::vector<int>& order, const std::vector<int>& local, in
     return n_rounds;
 }
 
+// Fewest rounds a tile allows: ceil(E / 32).  The greedy colourings above
+// leave most 1024-element tet tiles one round over it (33 rounds of ~31
+// elements), which costs the two-elements-per-lane kernels a fifth, half-empty
+// pair of rounds on one warp of every tile.  A tabu search repairs that: the
+// elements of the extra rounds go to the rounds with room and the fewest
+// clashes, then every step swaps a clashing element with the element of
+// another round (or moves it to a round with room) that lowers the number of
+// same-round element pairs sharing a node the most, and bars the reverse for
+// a few steps.  Ties and the element to repair are drawn from a fixed-seed
+// generator, so the plan stays a function of the mesh.  Returns false, with
+// round_of untouched, when no clash-free colouring is found in max_steps.
+bool tighten_rounds(int E, int ne, int nl, const std::vector<int>& local, std::vector<int>& round_of, int R,
+                    uint64_t seed, int max_steps = 4000) {
+    const int Rt = (E + kRound - 1) / kRound;
+    if (R <= Rt || Rt <= 0) return false;
+    uint64_t st = seed;
+    auto next = [&]() {  // splitmix64
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<int> ro(E, -1), size(Rt, 0);
+    std::vector<uint8_t> cnt((size_t)Rt * nl, 0);  // elements of round r on node n
+    auto at = [&](int r, int n) -> uint8_t& { return cnt[(size_t)r * nl + n]; };
+    auto put = [&](int e, int r) {
+        for (int a = 0; a < ne; ++a) ++at(r, local[e * ne + a]);
+        ++size[r];
+        ro[e] = r;
+    };
+    auto take = [&](int e) {
+        const int r = ro[e];
+        for (int a = 0; a < ne; ++a) --at(r, local[e * ne + a]);
+        --size[r];
+    };
+    auto seen = [&](int e, int r) {  // e's node clashes with the elements of round r
+        int c = 0;
+        for (int a = 0; a < ne; ++a) c += at(r, local[e * ne + a]);
+        return c;
+    };
+    for (int e = 0; e < E; ++e)
+        if (round_of[e] < Rt) put(e, round_of[e]);
+    for (int e = 0; e < E; ++e) {
+        if (round_of[e] < Rt) continue;
+        int best = -1, bc = 1 << 30;
+        for (int r = 0; r < Rt; ++r)
+            if (size[r] < kRound && seen(e, r) < bc) bc = seen(e, r), best = r;
+        put(e, best);  // total room is Rt * 32 >= E, so some round has room
+    }
+    std::vector<int> tabu((size_t)E * Rt, -1), conf(E), bad;
+    for (int step = 0; step < max_steps; ++step) {
+        bad.clear();
+        for (int e = 0; e < E; ++e) {
+            conf[e] = seen(e, ro[e]) - ne;
+            if (conf[e] > 0) bad.push_back(e);
+        }
+        if (bad.empty()) {
+            round_of = ro;
+            return true;
+        }
+        const int e = bad[next() % bad.size()];
+        const int r = ro[e];
+        const int* ev = &local[e * ne];
+        int best_f = -1, best_s = -1, best_d = 1 << 30;
+        uint64_t best_key = 0;
+        auto offer = [&](int f, int s, int d) {
+            const uint64_t key = next();
+            if (d < best_d || (d == best_d && key < best_key)) best_d = d, best_f = f, best_s = s, best_key = key;
+        };
+        for (int s = 0; s < Rt; ++s)  // moves into rounds with room
+            if (s != r && size[s] < kRound && tabu[(size_t)e * Rt + s] < step) offer(-1, s, seen(e, s) - conf[e]);
+        for (int f = 0; f < E; ++f) {
+            const int s = ro[f];
+            if (s == r || tabu[(size_t)e * Rt + s] >= step || tabu[(size_t)f * Rt + r] >= step) continue;
+            const int* fv = &local[f * ne];
+            int sh = 0;
+            for (int a = 0; a < ne; ++a)
+                for (int b = 0; b < ne; ++b) sh += ev[a] == fv[b];
+            offer(f, s, (seen(e, s) - sh) + (seen(f, r) - sh) - conf[e] - conf[f]);
+        }
+        if (best_s < 0) continue;
+        const int tenure = 7 + (int)(next() % 10);
+        take(e);
+        if (best_f >= 0) {
+            take(best_f);
+            put(best_f, r);
+            tabu[(size_t)best_f * Rt + best_s] = step + tenure;
+        }
+        put(e, best_s);
+        tabu[(size_t)e * Rt + r] = step + tenure;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // Bank-conflict-free arrangement of P1 rounds.
 //
@@ -494,6 +588,8 @@ void build_tile(const MeshInput& in, const int32_t* elems, int E, int pad, TileO
         out.err = "tile needs more than 128 rounds";
         return;
     }
+    if (tighten_rounds(E, ne, nl, local, round_of, R1, 0x5EEDull ^ (uint64_t)(uint32_t)elems[0]))
+        R1 = (E + kRound - 1) / kRound;
     // P1 tiles are relabelled and arranged so that the warp-wide
     // shared-memory gathers are free of bank conflicts
     const bool arrange = in.arrange && in.elem_type != 2;
