@@ -528,7 +528,7 @@ fem_status launch(fem_mesh* m, int dtype, int op, const void* u, const void* v, 
             void* q = nullptr;
             const size_t per_elem = m->etype == 2 ? 8 * fem::kHexLinVals : fem::kLinVals;
             size_t bytes = (size_t)m->plan.n_rounds() * 32 * per_elem * tsize;
-            if (pair_ok) bytes = std::max(bytes, (size_t)m->n_pairs * fem::kPairLinBytes);
+            if (pair_ok) bytes = std::max(bytes, (size_t)m->n_pairs * fem::pair_lin_bytes(m->etype));
             fem_status s = zalloc(m, &q, bytes, st);
             if (s != FEM_OK) return s;
             m->lin[pi] = q;

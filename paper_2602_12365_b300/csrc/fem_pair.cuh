@@ -31,12 +31,19 @@
 // synchronises between the two rounds.
 //
 // Four kernels share the body: the residual and the HVP at (u, v); the
-// linearisation pass (OP_LINEARIZE: per element F^-T, w mu, w (mu - lambda
-// ln J), w lambda at u, written as (A, B) pairs in pair-record order: 12
-// pairs per lane in 6 lane-major 16-byte chunks); and the HVP from that
-// stored linearisation (LIN: no u, no F, F^-1 or ln J; the lin block of a
-// pair travels in the same ring stage as its record), which is the PCG's
-// operator.  The HVPs can leave per-tile FP32-pair partials of v^T K v
+// linearisation pass (OP_LINEARIZE, at u, written as (A, B) pairs in
+// pair-record order, lane-major 16-byte chunks); and the HVP from that
+// stored linearisation (LIN), which is the PCG's operator.  The stored form
+// holds, per element, b_a = F^-T grad N_a for the vertices but the last, the
+// scaled metric w mu grad N_a . grad N_b, w (mu - lambda ln J) and w lambda.
+// With dF = sum_b dv_b (x) grad N_b (dv_b = v_b - v_last) the tangent of
+// the Neo-Hookean stress applied to grad N_a then reads
+//   w dP grad N_a = sum_b (w mu grad N_a . grad N_b) dv_b
+//                 + w (mu - lambda ln J) sum_b (b_a . dv_b) b_b
+//                 + w lambda (sum_b b_b . dv_b) b_a,
+// so the LIN HVP needs neither u, F, F^-1 and ln J nor the record's
+// geometry: its ring stage carries the record's node ids and the lin block
+// only.  The HVPs can leave per-tile FP32-pair partials of v^T K v
 // (vkv_tiles) for the PCG's fused dot product.
 #pragma once
 #include "fem_kernels.cuh"
@@ -70,14 +77,18 @@ __host__ __device__ constexpr int pair_rec_bytes(int et, bool mat) {
     return 32 * 16 * (1 + (et == 0 ? 3 : 5) + (mat ? 1 : 0));
 }
 
-// lin block of one pair record: 12 values x 2 elements x 32 lanes
-constexpr int kPairLinBytes = 32 * 16 * 6;
+// lin block of one pair record, in 16-byte chunks of two (A, B) pairs per
+// lane: b_a (D (NEN - 1) values), the metric's upper triangle, the two
+// scaled moduli and one zero -- tet 9 + 6 + 2 + 1 = 18 values, 9 chunks;
+// triangle 4 + 3 + 2 + 1 = 10 values, 5 chunks
+__host__ __device__ constexpr int pair_lin_chunks(int et) { return et == 0 ? 5 : 9; }
+__host__ __device__ constexpr int pair_lin_bytes(int et) { return 32 * 16 * pair_lin_chunks(et); }
 
-// bytes of the pair record a kernel copies: the geometry prefix (ids and
-// geometry), plus the moduli chunk unless the kernel reads the stored
-// linearisation (which carries the moduli)
+// bytes of the pair record a kernel copies: the ids and the geometry, plus
+// the moduli chunk when they vary per element; the HVP from the stored
+// linearisation copies the ids chunk only (the lin block carries the rest)
 __host__ __device__ constexpr int pair_copy_bytes(int et, bool mat, bool lin) {
-    return lin ? pair_rec_bytes(et, false) : pair_rec_bytes(et, mat);
+    return lin ? 32 * 16 : pair_rec_bytes(et, mat);
 }
 
 struct PairLayout {
@@ -110,7 +121,7 @@ __host__ __device__ inline PairLayout pair_layout(int et, int op, bool lin, int 
     o = align16(o + kMaxTilesPerCta * 16);
     L.off_tabp = o;
     o = align16(o + kMaxTilesPerCta * 4);
-    L.stage_bytes = copy_bytes + (lin ? kPairLinBytes : 0);
+    L.stage_bytes = copy_bytes + (lin ? pair_lin_bytes(et) : 0);
     L.off_ring = o = align16(o);
     o += kWarps * L.stage_bytes;
     L.off_bar = o = align16(o);
@@ -133,6 +144,9 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
     constexpr bool kLinz = OP == OP_LINEARIZE;     // writes the linearisation
     constexpr bool kHvp = OP == OP_HVP;
     constexpr bool kNeedU = !LIN, kNeedV = kHvp, kAcc = !kLinz;
+    constexpr int NLC = pair_lin_chunks(ET), kLinBytes = pair_lin_bytes(ET);
+    constexpr int NMET = NM1 * (NM1 + 1) / 2;  // the metric's upper triangle
+    static_assert(D * NM1 + NMET + 3 == 4 * NLC / 2, "the lin block: b_a, metric, two moduli, one zero");
     static_assert(OP == OP_RESIDUAL || OP == OP_HVP || OP == OP_LINEARIZE, "pair kernels: residual, HVP, linearise");
     static_assert(!LIN || kHvp, "the stored linearisation serves the HVP");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -258,9 +272,9 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
     auto issue_next = [&]() {
         const int64_t r = next_rec(cc);
         if (r < 0) return;
-        if constexpr (LIN)  // the record's geometry prefix, then its lin block; read once: evict first
+        if constexpr (LIN)  // the record's ids chunk, then its lin block; read once: evict first
             bulk_load2_hint(ring, p.prec + r * p.prec_bytes, (uint32_t)copy_bytes, ring + copy_bytes,
-                            glin + r * kPairLinBytes, (uint32_t)kPairLinBytes, rbar, l2_evict_first());
+                            glin + r * kLinBytes, (uint32_t)kLinBytes, rbar, l2_evict_first());
         else
             bulk_load(ring, p.prec + r * p.prec_bytes, (uint32_t)copy_bytes, rbar);
         ++issued;
@@ -329,15 +343,15 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
             const uint4 cw = reinterpret_cast<const uint4*>(st)[lane];
             float4 gc[5];
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) gc[c] = reinterpret_cast<const float4*>(st + 512 * (1 + c))[lane];
-#pragma unroll
-            for (int c = NCH; c < 5; ++c) gc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < 5; ++c)
+                gc[c] = (!LIN && c < NCH) ? reinterpret_cast<const float4*>(st + 512 * (1 + c))[lane]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 mc = make_float4(mu0, mu0, lam0, lam0);
             if (!LIN && p.has_mat) mc = reinterpret_cast<const float4*>(st + 512 * (1 + NCH))[lane];
-            float4 lc[LIN ? 6 : 1];
+            float4 lc[LIN ? NLC : 1];
             if constexpr (LIN) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) lc[c] = reinterpret_cast<const float4*>(st + copy_bytes + 512 * c)[lane];
+                for (int c = 0; c < NLC; ++c) lc[c] = reinterpret_cast<const float4*>(st + copy_bytes + 512 * c)[lane];
             }
             __syncwarp();
             if (lane == 0) {
@@ -370,57 +384,77 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
 #pragma unroll
                     for (int c = 0; c < D; ++c) dd[a][c] = mk2(ta[a][c] - ta[NM1][c], tb[a][c] - tb[NM1][c]);
             };
-            F2 g[NM1][D];
+            F2 g[NM1][D];  // grad N_a (zero for LIN, which reads no geometry)
 #pragma unroll
             for (int a = 0; a < NM1; ++a)
 #pragma unroll
                 for (int c = 0; c < D; ++c) g[a][c] = pair_of(gc, a * D + c);
             F2 P[D][D];
             F2 dF[D][D];
-            if constexpr (kNeedV) {
-                F2 dv[NM1][D];
-                diffs(sV, dv);
-                outer_sum<D, F2>(dv, g, NM1, dF);
-            }
+            F2 dv[NM1][D];
+            F2 f[NEN][D];  // forces on the vertices but the last (the last: minus their sum)
+            if constexpr (kNeedV) diffs(sV, dv);
+            if constexpr (kNeedV && !LIN) outer_sum<D, F2>(dv, g, NM1, dF);
             if constexpr (LIN) {
-                // dP = w mu dF + w (mu - lambda ln J) F^-T dF^T F^-T + w lambda tr(F^-1 dF) F^-T
-                // from the stored F^-T and scaled moduli (zero for empty or inverted elements)
+                // the forces from the stored b_a, metric and scaled moduli
+                // (all zero for empty or inverted elements)
                 auto lp = [&](int j) {
                     const float4 c = lc[j >> 1];
                     return (j & 1) ? mk2(c.z, c.w) : mk2(c.x, c.y);
                 };
-                F2 FiT[D][D];
+                F2 b[NM1][D];
 #pragma unroll
-                for (int i2 = 0; i2 < D; ++i2)
+                for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                    for (int j = 0; j < D; ++j) FiT[i2][j] = lp(i2 * D + j);
-                const F2 wmu = lp(9), c1 = lp(10), wlam = lp(11);
-                F2 trA = FiT[0][0] * dF[0][0];
+                    for (int c = 0; c < D; ++c) b[a][c] = lp(a * D + c);
+                F2 met[NM1][NM1];  // w mu grad N_a . grad N_b: diagonal, then (0,1), (0,2), (1,2)
+                {
+                    int q = D * NM1;
 #pragma unroll
-                for (int i2 = 0; i2 < D; ++i2)
+                    for (int a = 0; a < NM1; ++a) met[a][a] = lp(q++);
 #pragma unroll
-                    for (int j = 0; j < D; ++j)
-                        if (i2 + j > 0) trA = vfma(FiT[i2][j], dF[i2][j], trA);
-                F2 M[D][D];  // dF^T F^-T
+                    for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                for (int a = 0; a < D; ++a)
+                        for (int c = a + 1; c < NM1; ++c) met[a][c] = met[c][a] = lp(q++);
+                }
+                const F2 c1 = lp(D * NM1 + NMET), wlam = lp(D * NM1 + NMET + 1);
+                F2 m[NM1][NM1];  // b_a . dv_c
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        F2 t2 = dF[0][a] * FiT[0][j];
+                for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                        for (int l = 1; l < D; ++l) t2 = vfma(dF[l][a], FiT[l][j], t2);
-                        M[a][j] = t2;
+                    for (int c = 0; c < NM1; ++c) {
+                        F2 t2 = b[a][0] * dv[c][0];
+#pragma unroll
+                        for (int k = 1; k < D; ++k) t2 = vfma(b[a][k], dv[c][k], t2);
+                        m[a][c] = t2;
                     }
-                const F2 c2 = wlam * trA;
+                F2 tr = m[0][0];
 #pragma unroll
-                for (int i2 = 0; i2 < D; ++i2)
+                for (int a = 1; a < NM1; ++a) tr = tr + m[a][a];
+                const F2 sl = wlam * tr;
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        F2 B = FiT[i2][0] * M[0][j];
+                for (int a = 0; a < NM1; ++a) {
+                    F2 n[NM1];
 #pragma unroll
-                        for (int a = 1; a < D; ++a) B = vfma(FiT[i2][a], M[a][j], B);
-                        P[i2][j] = vfma(c2, FiT[i2][j], vfma(c1, B, wmu * dF[i2][j]));
+                    for (int c = 0; c < NM1; ++c) n[c] = c1 * m[a][c];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        F2 t2 = sl * b[a][k];
+#pragma unroll
+                        for (int c = 0; c < NM1; ++c) t2 = vfma(met[a][c], dv[c][k], vfma(n[c], b[c][k], t2));
+                        f[a][k] = t2;
                     }
+                }
+                if (want_vkv) {  // v^T K v of both halves: sum_a dv_a . f_a (the forces sum to zero)
+                    F2 e = dv[0][0] * f[0][0];
+#pragma unroll
+                    for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                        for (int k = 0; k < D; ++k)
+                            if (a + k > 0) e = vfma(dv[a][k], f[a][k], e);
+                    ff_add(vk_hi, vk_lo, e.v.x);
+                    ff_add(vk_hi, vk_lo, e.v.y);
+                }
             } else {
                 F2 du[NM1][D];
                 diffs(sU, du);
@@ -435,24 +469,40 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
                 const F2 mu = mk2(mc.x, mc.y), lam = mk2(mc.z, mc.w);
                 const F2 wmu = wdJ * mu, wlam = wdJ * lam;
                 if constexpr (kLinz) {
-                    // F^-T, w mu, w (mu - lambda ln J), w lambda: 12 pairs in 6
-                    // lane-major chunks of the pair's lin block (2D uses the
-                    // first four F^-T slots)
-                    F2 o[12];
+                    // b_a = F^-T grad N_a, the metric w mu grad N_a . grad N_b,
+                    // w (mu - lambda ln J), w lambda and a zero, as the pair's
+                    // lin block (lane-major chunks); inverted halves store zeros
+                    F2 o[2 * NLC];
+                    int q = 0;
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) o[q] = mk2(0.f, 0.f);
+                    for (int a = 0; a < NM1; ++a)
 #pragma unroll
-                    for (int i2 = 0; i2 < D; ++i2)
+                        for (int c = 0; c < D; ++c) {
+                            // row c of F^-T = I + G, applied to grad N_a
+                            F2 t2 = g[a][c];
 #pragma unroll
-                        for (int j = 0; j < D; ++j)
-                            o[i2 * D + j] = (i2 == j) ? kin.G[i2][j] + mk2(1.f, 1.f) : kin.G[i2][j];
-                    o[9] = wmu;
-                    o[10] = wdJ * (mu - lam * kin.lnJ);
-                    o[11] = wlam;
+                            for (int k = 0; k < D; ++k) t2 = vfma(kin.G[c][k], g[a][k], t2);
+                            o[q++] = vsel(kin.ok, t2, 0.f);
+                        }
+                    auto dot_g = [&](int a, int c) {
+                        F2 t2 = g[a][0] * g[c][0];
+#pragma unroll
+                        for (int k = 1; k < D; ++k) t2 = vfma(g[a][k], g[c][k], t2);
+                        return wmu * t2;
+                    };
+#pragma unroll
+                    for (int a = 0; a < NM1; ++a) o[q++] = dot_g(a, a);
+#pragma unroll
+                    for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                        for (int c = a + 1; c < NM1; ++c) o[q++] = dot_g(a, c);
+                    o[q++] = wdJ * (mu - lam * kin.lnJ);
+                    o[q++] = wlam;
+                    o[q++] = mk2(0.f, 0.f);
                     float4* dst = reinterpret_cast<float4*>(static_cast<unsigned char*>(p.lin) +
-                                                            (int64_t)(p0 + k) * kPairLinBytes) + lane;
+                                                            (int64_t)(p0 + k) * kLinBytes) + lane;
 #pragma unroll
-                    for (int c = 0; c < 6; ++c)
+                    for (int c = 0; c < NLC; ++c)
                         dst[32 * c] = make_float4(o[2 * c].v.x, o[2 * c].v.y, o[2 * c + 1].v.x, o[2 * c + 1].v.y);
                 } else if constexpr (kHvp) {
                     tangent<D, F2>(dF, kin, wmu, wlam, P);
@@ -461,28 +511,29 @@ __device__ __forceinline__ void pair_body(const KParams& p) {
                 }
             }
             if constexpr (kAcc) {
-                if constexpr (kHvp) {
-                    if (want_vkv) {  // w dP : dF of both halves
-                        F2 e = P[0][0] * dF[0][0];
+                if constexpr (!LIN) {
+                    if constexpr (kHvp) {
+                        if (want_vkv) {  // w dP : dF of both halves
+                            F2 e = P[0][0] * dF[0][0];
 #pragma unroll
-                        for (int i2 = 0; i2 < D; ++i2)
+                            for (int i2 = 0; i2 < D; ++i2)
 #pragma unroll
-                            for (int j = 0; j < D; ++j)
-                                if (i2 + j > 0) e = vfma(P[i2][j], dF[i2][j], e);
-                        ff_add(vk_hi, vk_lo, e.v.x);
-                        ff_add(vk_hi, vk_lo, e.v.y);
+                                for (int j = 0; j < D; ++j)
+                                    if (i2 + j > 0) e = vfma(P[i2][j], dF[i2][j], e);
+                            ff_add(vk_hi, vk_lo, e.v.x);
+                            ff_add(vk_hi, vk_lo, e.v.y);
+                        }
                     }
+#pragma unroll
+                    for (int a = 0; a < NM1; ++a)
+#pragma unroll
+                        for (int c = 0; c < D; ++c) {
+                            F2 s2 = P[c][0] * g[a][0];
+#pragma unroll
+                            for (int j = 1; j < D; ++j) s2 = vfma(P[c][j], g[a][j], s2);
+                            f[a][c] = s2;
+                        }
                 }
-                F2 f[NEN][D];
-#pragma unroll
-                for (int a = 0; a < NM1; ++a)
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        F2 s2 = P[c][0] * g[a][0];
-#pragma unroll
-                        for (int j = 1; j < D; ++j) s2 = vfma(P[c][j], g[a][j], s2);
-                        f[a][c] = s2;
-                    }
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
                     F2 s2 = -f[0][c];
