@@ -84,6 +84,34 @@ def test_random_moduli_mixed_matches_oracle():
     assert _rel(ug, uo) <= 1e-6
 
 
+def _jittered(m, amp, seed):
+    """Interior nodes moved by up to amp h: the hexahedra stop being
+    parallelepipeds."""
+    g = mg.grid_index(m)
+    interior = np.all((g > 0) & (g < m.n), axis=1)
+    rng = np.random.default_rng(seed)
+    m.coords = m.coords.copy()
+    m.coords[interior] += amp / m.n * (2 * rng.random(m.coords[interior].shape) - 1)
+    return m
+
+
+@pytest.mark.parametrize("shape", ["affine", "jittered"])
+@pytest.mark.parametrize("cg_dtype", [torch.float64, torch.float32])
+def test_hex_load_steps_match_oracle(shape, cg_dtype):
+    """Q1 load steps through the per-point stored linearisation against the
+    oracle, on a grid of parallelepipeds (J the same at every Gauss point)
+    and on a jittered grid (J varying between the points)."""
+    m = mg.workload_hex(4, seed=2)
+    if shape == "jittered":
+        m = _jittered(m, 0.15, 5)
+    steps = [0.05, 0.1]
+    ug, sg, _ = _gpu_path(m, steps, cg_dtype)
+    uo, _ = _oracle_path(m, steps)
+    assert _rel(ug, uo) <= 1e-6
+    for a in sg:
+        assert a["status"] == 0 and a["r_norm"] <= 1e-8 * a["r0_norm"]
+
+
 def _lateral_stretch(dim, delta):
     if dim == 2:
         f = lambda b: MU * (b - 1 / b) + LAM * np.log((1 + delta) * b) / b

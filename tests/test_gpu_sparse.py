@@ -144,13 +144,26 @@ def test_spmv_matches_host_csr(kind, dt):
     assert gm.sync_status() == 0
 
 
-@pytest.mark.parametrize("kind,n,tile", [("hex", 1, 0), ("hex", 4, 16), ("tet", 1, 0), ("tet", 3, 40)])
+def _jittered_hex(n, seed):
+    m = mg.workload_hex(n, seed=seed)
+    g = mg.grid_index(m)
+    interior = np.all((g > 0) & (g < m.n), axis=1)
+    rng = np.random.default_rng(seed)
+    m.coords = m.coords.copy()
+    m.coords[interior] += 0.15 / m.n * (2 * rng.random(m.coords[interior].shape) - 1)
+    return m
+
+
+@pytest.mark.parametrize("kind,n,tile", [("hex", 1, 0), ("hex", 4, 16), ("hex_jittered", 4, 16), ("tet", 1, 0),
+                                         ("tet", 3, 40)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_assemble_edge_plans_match_oracle(kind, n, tile, precision, tol):
     """Algorithm 2 through the stored linearisation on plans with a single
     element (one lane of one round) and with many small tiles (partial
-    rounds, most nodes shared between tiles)."""
-    m = {"hex": lambda: mg.workload_hex(n, seed=4), "tet": lambda: mg.workload_tet(n, seed=4, random_moduli=4)}[kind]()
+    rounds, most nodes shared between tiles); Q1 on parallelepipeds and on a
+    jittered grid (J varying between the Gauss points)."""
+    m = {"hex": lambda: mg.workload_hex(n, seed=4), "hex_jittered": lambda: _jittered_hex(n, 4),
+         "tet": lambda: mg.workload_tet(n, seed=4, random_moduli=4)}[kind]()
     gm = Mesh.from_fixture(m, precision=precision, tile_elems=tile)
     dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.as_tensor(_state(m), dtype=dt, device="cuda")
