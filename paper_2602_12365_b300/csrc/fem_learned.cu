@@ -13,9 +13,12 @@
 // Inference runs the three layers on the tensor cores with mma.sync
 // m16n8k16 (one warp per 16 nodes, the layers chained in registers: the
 // accumulator fragments of two adjacent 8-column tiles are the next layer's
-// 16-wide A fragment).  The network is 3.7 GFLOP per call on 274k nodes and
-// is bound by reading its 26 MB of features, so the warp-level MMA is
-// enough; the epilogue forms M_i per node.
+// 16-wide A fragment); the epilogue forms M_i per node.  In the Newton
+// solve's preconditioner build, features, network and block map run in one
+// kernel (lp_precond_kernel), the features staying in shared memory.  The
+// network is 3.7 GFLOP per call on 274k nodes; what bounds the kernel is the
+// per-node scalar work around it (neighbour sums, logarithms, 128 SiLUs per
+// node), so the warp-level MMA is enough.
 //
 // Training minimises ||H M r - r||^2 / ||r||^2 over states u and residuals
 // r of the method's own Newton solves (H = M K(u) M, masked): the forward
@@ -83,9 +86,15 @@ fem_status fail(fem_status s, const std::string& msg) { return femi::set_error(s
 // ---------------------------------------------------------------------------
 // shared device helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float silu(float x) { return x / (1.0f + expf(-x)); }
+// SiLU of the hidden layers with the fast exponential and division
+// intrinsics (about 1e-6 relative; each result is rounded to BF16 at once,
+// a 4e-3 step): the network is issue-bound on these, 128 per node.  Below
+// -87 the denominator overflows and the quotient is zero, as SiLU is there
+// to FP32 precision.  Inference and the training's recomputed forward call
+// the same function.
+__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float dsilu(float x) {
-    const float s = 1.0f / (1.0f + expf(-x));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-x));
     return s * (1.0f + x * (1.0f - s));
 }
 __device__ __forceinline__ float softplus(float x) { return x > 20.0f ? x : log1pf(expf(x)); }
@@ -195,56 +204,107 @@ __device__ __forceinline__ void lp_block(const float (&Di)[9], uint8_t mask, con
 //   27 ln mean mu, 28 ln(mean lambda / mean mu), 29 valence / 24
 //   [30,33) Dirichlet bits, [33,36) ln(D_i,cc / s_i)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kVecT) lp_features_kernel(int64_t nn, const float* D, const int64_t* ptr,
+// the 36 features of node n as 18 BF16 pairs (all zero when D_n has no
+// positive trace), and D_n itself.  The neighbours' blocks are loaded
+// kNb at a time (their loads in flight together) and added in list order.
+constexpr int kNb = 4;
+__device__ __forceinline__ void lp_node_features(int64_t n, const float* D, const float* D8, const int64_t* ptr,
+                                                 const int32_t* idx, const float* stats, const uint8_t* node_mask,
+                                                 uint32_t (&xw)[kIn / 2], float (&Di)[9]) {
+    float f[kIn];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Di[k] = D[n * 9 + k];
+    const float s = (Di[0] + Di[4] + Di[8]) * (1.0f / 3.0f);
+    const bool ok = s > 0.0f && isfinite(s);
+    const float is = ok ? 1.0f / s : 0.0f;
+    float mean[9] = {}, dev[9] = {};
+    const int64_t j0 = ptr[n], j1 = ptr[n + 1];
+    // one pass over the neighbour list: kNb blocks in flight, then their adds
+    // (dv = 1: sum of D_j; dv = 2: sum of |D_j - mean|)
+    auto pass = [&](int dv) {
+        for (int64_t j = j0; j < j1; j += kNb) {
+            int32_t q[kNb];
+#pragma unroll
+            for (int b = 0; b < kNb; ++b) q[b] = j + b < j1 ? idx[j + b] : -1;
+            // the nodal blocks are symmetric (the block diagonal is written
+            // from its six distinct entries): D8 holds those, 16-byte aligned
+            float t[kNb][9];
+#pragma unroll
+            for (int b = 0; b < kNb; ++b) {
+                float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+                if (q[b] >= 0) {
+                    lo = reinterpret_cast<const float4*>(D8)[2 * (int64_t)q[b]];
+                    hi = reinterpret_cast<const float4*>(D8)[2 * (int64_t)q[b] + 1];
+                }
+                t[b][0] = lo.x, t[b][1] = lo.y, t[b][2] = lo.z;
+                t[b][3] = lo.y, t[b][4] = lo.w, t[b][5] = hi.x;
+                t[b][6] = lo.z, t[b][7] = hi.x, t[b][8] = hi.y;
+            }
+#pragma unroll
+            for (int b = 0; b < kNb; ++b) {
+                if (q[b] < 0) break;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    if (dv == 1)
+                        mean[k] += t[b][k];
+                    else
+                        dev[k] += fabsf(t[b][k] - mean[k]);
+                }
+            }
+        }
+    };
+    pass(1);
+    const float inb = j1 > j0 ? 1.0f / (float)(j1 - j0) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) mean[k] *= inb;
+    pass(2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        f[k] = Di[k] * is;
+        f[9 + k] = mean[k] * is;
+        f[18 + k] = dev[k] * inb * is;
+    }
+    // block ratios span orders of magnitude at boundary and
+    // high-contrast nodes: compress them as sign(x) ln(1 + |x|), by the
+    // branch-free FP32 logarithm (exponent split and artanh series, a few
+    // ulps for every finite |x|; the feature is then rounded to BF16)
+#pragma unroll
+    for (int k = 0; k < 27; ++k) f[k] = copysignf(fem::vlog1p_bf(fabsf(f[k])), f[k]);
+    f[27] = stats[n * 3 + 0];
+    f[28] = stats[n * 3 + 1];
+    f[29] = stats[n * 3 + 2];
+    const uint8_t m = node_mask[n];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f[30 + c] = ((m >> c) & 1) ? 1.0f : 0.0f;
+        f[33 + c] = ok ? logf(Di[c * 4] * is) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kIn; k += 2) xw[k / 2] = ok ? pack_bf16(f[k], f[k + 1]) : 0u;
+}
+
+// D8 of every node from its block in D
+__global__ void __launch_bounds__(kVecT) lp_pack_kernel(int64_t nn, const float* D, float* D8) {
+    for (int64_t n = blockIdx.x * (int64_t)kVecT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVecT) {
+        const float* b = D + n * 9;
+        reinterpret_cast<float4*>(D8)[2 * n] = make_float4(b[0], b[1], b[2], b[4]);
+        reinterpret_cast<float4*>(D8)[2 * n + 1] = make_float4(b[5], b[8], 0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(kVecT) lp_features_kernel(int64_t nn, const float* D, const float* D8,
+                                                            const int64_t* ptr,
                                                             const int32_t* idx, const float* stats,
                                                             const uint8_t* node_mask, __nv_bfloat16* X) {
     for (int64_t n = blockIdx.x * (int64_t)kVecT + threadIdx.x; n < nn; n += (int64_t)gridDim.x * kVecT) {
-        float f[kIn];
+        uint32_t xw[kIn / 2];
         float Di[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Di[k] = D[n * 9 + k];
-        const float s = (Di[0] + Di[4] + Di[8]) * (1.0f / 3.0f);
-        const bool ok = s > 0.0f && isfinite(s);
-        const float is = ok ? 1.0f / s : 0.0f;
-        float mean[9] = {}, dev[9] = {};
-        const int64_t j0 = ptr[n], j1 = ptr[n + 1];
-        for (int64_t j = j0; j < j1; ++j) {
-            const float* Dj = D + (int64_t)idx[j] * 9;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) mean[k] += Dj[k];
-        }
-        const float inb = j1 > j0 ? 1.0f / (float)(j1 - j0) : 0.0f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) mean[k] *= inb;
-        for (int64_t j = j0; j < j1; ++j) {
-            const float* Dj = D + (int64_t)idx[j] * 9;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) dev[k] += fabsf(Dj[k] - mean[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            f[k] = Di[k] * is;
-            f[9 + k] = mean[k] * is;
-            f[18 + k] = dev[k] * inb * is;
-        }
-        // block ratios span orders of magnitude at boundary and
-        // high-contrast nodes: compress them as sign(x) ln(1 + |x|)
-#pragma unroll
-        for (int k = 0; k < 27; ++k) f[k] = copysignf(log1pf(fabsf(f[k])), f[k]);
-        f[27] = stats[n * 3 + 0];
-        f[28] = stats[n * 3 + 1];
-        f[29] = stats[n * 3 + 2];
-        const uint8_t m = node_mask[n];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            f[30 + c] = ((m >> c) & 1) ? 1.0f : 0.0f;
-            f[33 + c] = ok ? logf(Di[c * 4] * is) : 0.0f;
-        }
+        lp_node_features(n, D, D8, ptr, idx, stats, node_mask, xw, Di);
         uint32_t* dst = reinterpret_cast<uint32_t*>(X + n * kInPad);
 #pragma unroll
-        for (int k = 0; k < kIn; k += 2) dst[k / 2] = ok ? pack_bf16(f[k], f[k + 1]) : 0u;
+        for (int k = 0; k < kIn / 2; ++k) dst[k] = xw[k];
 #pragma unroll
-        for (int k = kIn; k < kInPad; k += 2) dst[k / 2] = 0u;
+        for (int k = kIn / 2; k < kInPad / 2; ++k) dst[k] = 0u;
     }
 }
 
@@ -257,6 +317,67 @@ struct InferW {
 };
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// The network on one tile of 16 nodes (one warp, mma.sync m16n8k16): a1 holds
+// the tile's layer-1 A fragments (k blocks of 16 over the 48 padded inputs),
+// the weights and biases are in shared memory; o3 gets the lane's outputs
+// (rows g and g + 8, columns 2t and 2t + 1; columns 6 and 7 are zero rows).
+// The accumulator fragments of two adjacent 8-column tiles are the next
+// layer's 16-wide A fragment, so the layers chain in registers.
+__device__ __forceinline__ void lp_mlp16(const uint32_t (&a1)[kInPad / 16][4], const __nv_bfloat16* sW1,
+                                         const __nv_bfloat16* sW2, const __nv_bfloat16* sW3, const float* sb1,
+                                         const float* sb2, const float* sb3, int g, int t, float (&o3)[4]) {
+    // layer 1: [16 x 48] x [48 x 64]
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j][0] = acc[j][2] = sb1[8 * j + 2 * t];
+        acc[j][1] = acc[j][3] = sb1[8 * j + 2 * t + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < kInPad / 16; ++kk)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat16* wr = sW1 + (8 * j + g) * kS1 + 16 * kk + 2 * t;
+            mma_bf16(acc[j], a1[kk], ld32(wr), ld32(wr + 8));
+        }
+    // SiLU, BF16: the accumulators of n-tiles 2kk, 2kk+1 are layer 2's A fragment kk
+    uint32_t ah[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        ah[kk][0] = pack_bf16(silu(acc[2 * kk][0]), silu(acc[2 * kk][1]));
+        ah[kk][1] = pack_bf16(silu(acc[2 * kk][2]), silu(acc[2 * kk][3]));
+        ah[kk][2] = pack_bf16(silu(acc[2 * kk + 1][0]), silu(acc[2 * kk + 1][1]));
+        ah[kk][3] = pack_bf16(silu(acc[2 * kk + 1][2]), silu(acc[2 * kk + 1][3]));
+    }
+    // layer 2: [16 x 64] x [64 x 64]
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j][0] = acc[j][2] = sb2[8 * j + 2 * t];
+        acc[j][1] = acc[j][3] = sb2[8 * j + 2 * t + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat16* wr = sW2 + (8 * j + g) * kS2 + 16 * kk + 2 * t;
+            mma_bf16(acc[j], ah[kk], ld32(wr), ld32(wr + 8));
+        }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        ah[kk][0] = pack_bf16(silu(acc[2 * kk][0]), silu(acc[2 * kk][1]));
+        ah[kk][1] = pack_bf16(silu(acc[2 * kk][2]), silu(acc[2 * kk][3]));
+        ah[kk][2] = pack_bf16(silu(acc[2 * kk + 1][0]), silu(acc[2 * kk + 1][1]));
+        ah[kk][3] = pack_bf16(silu(acc[2 * kk + 1][2]), silu(acc[2 * kk + 1][3]));
+    }
+    // layer 3: [16 x 64] x [64 x 8] (outputs 6, 7 are zero rows)
+    o3[0] = sb3[2 * t], o3[1] = sb3[2 * t + 1], o3[2] = sb3[2 * t], o3[3] = sb3[2 * t + 1];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const __nv_bfloat16* wr = sW3 + g * kS2 + 16 * kk + 2 * t;
+        mma_bf16(o3, ah[kk], ld32(wr), ld32(wr + 8));
+    }
+}
 
 __global__ void __launch_bounds__(kInferThreads) lp_infer_kernel(int64_t nn, const __nv_bfloat16* X, const float* D,
                                                                  const uint8_t* node_mask, InferW W, float* Minv) {
@@ -278,62 +399,17 @@ __global__ void __launch_bounds__(kInferThreads) lp_infer_kernel(int64_t nn, con
     for (int64_t tile = (int64_t)blockIdx.x * (kInferThreads / 32) + warp; tile < n_tiles;
          tile += (int64_t)gridDim.x * (kInferThreads / 32)) {
         const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        // layer 1: [16 x 48] x [48 x 64]
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            acc[j][0] = acc[j][2] = sb1[8 * j + 2 * t];
-            acc[j][1] = acc[j][3] = sb1[8 * j + 2 * t + 1];
-        }
+        // layer 1's A fragments of the tile from the features in global memory
+        uint32_t a1[kInPad / 16][4];
 #pragma unroll
         for (int kk = 0; kk < kInPad / 16; ++kk) {
-            uint32_t a[4];
-            a[0] = r0 < nn ? ld32(X + r0 * kInPad + 16 * kk + 2 * t) : 0u;
-            a[1] = r1 < nn ? ld32(X + r1 * kInPad + 16 * kk + 2 * t) : 0u;
-            a[2] = r0 < nn ? ld32(X + r0 * kInPad + 16 * kk + 8 + 2 * t) : 0u;
-            a[3] = r1 < nn ? ld32(X + r1 * kInPad + 16 * kk + 8 + 2 * t) : 0u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat16* wr = sW1 + (8 * j + g) * kS1 + 16 * kk + 2 * t;
-                mma_bf16(acc[j], a, ld32(wr), ld32(wr + 8));
-            }
+            a1[kk][0] = r0 < nn ? ld32(X + r0 * kInPad + 16 * kk + 2 * t) : 0u;
+            a1[kk][1] = r1 < nn ? ld32(X + r1 * kInPad + 16 * kk + 2 * t) : 0u;
+            a1[kk][2] = r0 < nn ? ld32(X + r0 * kInPad + 16 * kk + 8 + 2 * t) : 0u;
+            a1[kk][3] = r1 < nn ? ld32(X + r1 * kInPad + 16 * kk + 8 + 2 * t) : 0u;
         }
-        // SiLU, BF16: the accumulators of n-tiles 2kk, 2kk+1 are layer 2's A fragment kk
-        uint32_t ah[4][4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            ah[kk][0] = pack_bf16(silu(acc[2 * kk][0]), silu(acc[2 * kk][1]));
-            ah[kk][1] = pack_bf16(silu(acc[2 * kk][2]), silu(acc[2 * kk][3]));
-            ah[kk][2] = pack_bf16(silu(acc[2 * kk + 1][0]), silu(acc[2 * kk + 1][1]));
-            ah[kk][3] = pack_bf16(silu(acc[2 * kk + 1][2]), silu(acc[2 * kk + 1][3]));
-        }
-        // layer 2: [16 x 64] x [64 x 64]
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            acc[j][0] = acc[j][2] = sb2[8 * j + 2 * t];
-            acc[j][1] = acc[j][3] = sb2[8 * j + 2 * t + 1];
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat16* wr = sW2 + (8 * j + g) * kS2 + 16 * kk + 2 * t;
-                mma_bf16(acc[j], ah[kk], ld32(wr), ld32(wr + 8));
-            }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            ah[kk][0] = pack_bf16(silu(acc[2 * kk][0]), silu(acc[2 * kk][1]));
-            ah[kk][1] = pack_bf16(silu(acc[2 * kk][2]), silu(acc[2 * kk][3]));
-            ah[kk][2] = pack_bf16(silu(acc[2 * kk + 1][0]), silu(acc[2 * kk + 1][1]));
-            ah[kk][3] = pack_bf16(silu(acc[2 * kk + 1][2]), silu(acc[2 * kk + 1][3]));
-        }
-        // layer 3: [16 x 64] x [64 x 8] (outputs 6, 7 are zero rows)
-        float o3[4] = {sb3[2 * t], sb3[2 * t + 1], sb3[2 * t], sb3[2 * t + 1]};
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const __nv_bfloat16* wr = sW3 + g * kS2 + 16 * kk + 2 * t;
-            mma_bf16(o3, ah[kk], ld32(wr), ld32(wr + 8));
-        }
+        float o3[4];
+        lp_mlp16(a1, sW1, sW2, sW3, sb1, sb2, sb3, g, t, o3);
         sOut[warp][g][2 * t] = o3[0];
         sOut[warp][g][2 * t + 1] = o3[1];
         sOut[warp][g + 8][2 * t] = o3[2];
@@ -349,6 +425,78 @@ __global__ void __launch_bounds__(kInferThreads) lp_infer_kernel(int64_t nn, con
             lp_block(Di, node_mask[n], o, Minv + n * 9);
         }
         __syncwarp();
+    }
+}
+
+// Features, network and block map in one pass (the preconditioner build of
+// a Newton iteration): each warp takes 32 nodes at a time, one per lane; the
+// lane's features go to its row of the warp's tile in shared memory (BF16,
+// zero-padded to 48 inputs), the network runs on the tile's two 16-node
+// halves, and each lane applies the block map to its own node with the D_n
+// it loaded for the features.  The features never go through global memory;
+// the arithmetic is that of lp_features_kernel followed by lp_infer_kernel.
+constexpr int kPrecondThreads = 128;
+__global__ void __launch_bounds__(kPrecondThreads, 5) lp_precond_kernel(int64_t nn, const float* D, const float* D8,
+                                                                     const int64_t* ptr,
+                                                                     const int32_t* idx, const float* stats,
+                                                                     const uint8_t* node_mask, InferW W,
+                                                                     float* Minv) {
+    constexpr int kWarps_ = kPrecondThreads / 32;
+    constexpr int kRowWords = kS1 / 2;  // 28 words per row: conflict-free fragment loads
+    __shared__ __align__(16) __nv_bfloat16 sW[kBf16Elems];
+    __shared__ float sB[kBiasFloats];
+    __shared__ __align__(16) uint32_t sX[kWarps_][32][kRowWords];
+    __shared__ float sOut[kWarps_][32][8];
+    for (int i = threadIdx.x; i < kBf16Elems; i += kPrecondThreads) sW[i] = W.w[i];
+    for (int i = threadIdx.x; i < kBiasFloats; i += kPrecondThreads) sB[i] = W.b[i];
+    __syncthreads();
+    const __nv_bfloat16* sW1 = sW;
+    const __nv_bfloat16* sW2 = sW + kH * kS1;
+    const __nv_bfloat16* sW3 = sW2 + kH * kS2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t n_groups = (nn + 31) / 32;
+    for (int64_t grp = (int64_t)blockIdx.x * kWarps_ + warp; grp < n_groups; grp += (int64_t)gridDim.x * kWarps_) {
+        const int64_t n = grp * 32 + lane;
+        uint32_t* row = sX[warp][lane];
+        float Di[9] = {};
+        if (n < nn) {
+            uint32_t xw[kIn / 2];
+            lp_node_features(n, D, D8, ptr, idx, stats, node_mask, xw, Di);
+#pragma unroll
+            for (int k = 0; k < kIn / 2; ++k) row[k] = xw[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kIn / 2; ++k) row[k] = 0u;
+        }
+#pragma unroll
+        for (int k = kIn / 2; k < kInPad / 2; ++k) row[k] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // rows 16h .. 16h + 15 of the tile
+            uint32_t a1[kInPad / 16][4];
+#pragma unroll
+            for (int kk = 0; kk < kInPad / 16; ++kk) {
+                a1[kk][0] = sX[warp][16 * h + g][8 * kk + t];
+                a1[kk][1] = sX[warp][16 * h + g + 8][8 * kk + t];
+                a1[kk][2] = sX[warp][16 * h + g][8 * kk + 4 + t];
+                a1[kk][3] = sX[warp][16 * h + g + 8][8 * kk + 4 + t];
+            }
+            float o3[4];
+            lp_mlp16(a1, sW1, sW2, sW3, sB, sB + kH, sB + 2 * kH, g, t, o3);
+            sOut[warp][16 * h + g][2 * t] = o3[0];
+            sOut[warp][16 * h + g][2 * t + 1] = o3[1];
+            sOut[warp][16 * h + g + 8][2 * t] = o3[2];
+            sOut[warp][16 * h + g + 8][2 * t + 1] = o3[3];
+        }
+        __syncwarp();
+        if (n < nn) {
+            float o[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = sOut[warp][lane][k];
+            lp_block(Di, node_mask[n], o, Minv + n * 9);
+        }
+        __syncwarp();  // the tile's rows and outputs are rewritten by the next group
     }
 }
 
@@ -702,6 +850,9 @@ struct LpMeshData {
     int32_t* idx = nullptr;
     float* stats = nullptr;
     float* D = nullptr;
+    // the blocks' distinct entries D00 D01 D02 D11 D12 D22 and two zeros per
+    // node: two 16-byte loads per neighbour in the features
+    float* D8 = nullptr;
     __nv_bfloat16* X = nullptr;
     float *Minv = nullptr, *z = nullptr, *q = nullptr, *e = nullptr;
     float* partial = nullptr;  // [kGradBlocks * kParams]
@@ -766,6 +917,7 @@ fem_status ensure_mesh(fem_mesh* m, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(d->stats, m->node_stats.data(), m->node_stats.size() * sizeof(float),
                              cudaMemcpyHostToDevice, st));
     FEM_TRY(dalloc(d, &d->D, (size_t)nn * 9));
+    FEM_TRY(dalloc(d, &d->D8, (size_t)nn * 8));
     FEM_TRY(dalloc(d, &d->X, (size_t)nn * kInPad));
     FEM_TRY(dalloc(d, &d->Minv, (size_t)nn * 9));
     FEM_TRY(dalloc(d, &d->z, (size_t)nn * 3));
@@ -783,7 +935,9 @@ fem_status features(fem_mesh* m, const float* u, cudaStream_t st) {
     FEM_TRY(ensure_mesh(m, st));
     femi::LpMeshData* d = m->lp;
     FEM_TRY(femi::run_op(m, FEM_F32, fem::OP_BLOCKDIAG, u, nullptr, d->D, nullptr, 0, st, nullptr));
-    lp_features_kernel<<<grid_for(d->nn, 1184), kVecT, 0, st>>>(d->nn, d->D, d->ptr, d->idx, d->stats, m->node_mask, d->X);
+    lp_pack_kernel<<<grid_for(d->nn, 1184), kVecT, 0, st>>>(d->nn, d->D, d->D8);
+    lp_features_kernel<<<grid_for(d->nn, 1184), kVecT, 0, st>>>(d->nn, d->D, d->D8, d->ptr, d->idx, d->stats,
+                                                                  m->node_mask, d->X);
     CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -843,11 +997,21 @@ fem_status upload_params(fem_lp* lp, const float* host, cudaStream_t st) {
 }  // namespace
 
 namespace femi {
+// the blocks M_n at u: the block diagonal, then features, network and block
+// map in one kernel
 fem_status lp_precondition(const void* lpv, fem_mesh* m, const float* u, float* Minv, cudaStream_t st) {
     const fem_lp* lp = static_cast<const fem_lp*>(lpv);
     FEM_TRY(check_lp(lp));
-    FEM_TRY(features(m, u, st));
-    return infer(lp, m, Minv, st);
+    FEM_TRY(ensure_mesh(m, st));
+    LpMeshData* d = m->lp;
+    FEM_TRY(run_op(m, FEM_F32, fem::OP_BLOCKDIAG, u, nullptr, d->D, nullptr, 0, st, nullptr));
+    lp_pack_kernel<<<grid_for(d->nn, 1184), kVecT, 0, st>>>(d->nn, d->D, d->D8);
+    const int64_t groups = (d->nn + 31) / 32;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + 3) / 4, 148 * 5));
+    lp_precond_kernel<<<grid, kPrecondThreads, 0, st>>>(d->nn, d->D, d->D8, d->ptr, d->idx, d->stats, m->node_mask,
+                                                       InferW{lp->wb, lp->bb}, Minv);
+    CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
 }
 }  // namespace femi
 
