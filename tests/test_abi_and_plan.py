@@ -98,6 +98,19 @@ def test_plan_is_deterministic(lib):
         np.testing.assert_array_equal(x, y)
 
 
+def test_round_repair_is_deterministic(lib):
+    """The tabu repair draws from a generator seeded by each tile's first
+    element, and tiles are built on several host threads: two plans of the
+    same mesh are identical, round for round and lane for lane."""
+    from paper_2602_12365_b300.fem import plan_partition
+    m = mg.tet_mesh(16, jitter_seed=2)
+    a = plan_partition(m.elem_type, m.coords, m.conn, 0)
+    b = plan_partition(m.elem_type, m.coords, m.conn, 0)
+    assert a[4]["max_rounds"] == 32  # every tile repaired to the floor
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("n,tile", [(16, 512), (16, 256), (8, 256)])
 def test_structured_hex_rounds_are_full(lib, n, tile):
     """On a structured Q1 grid whose tiles are boxes of at least 256 cells
