@@ -588,8 +588,14 @@ void build_tile(const MeshInput& in, const int32_t* elems, int E, int pad, TileO
         out.err = "tile needs more than 128 rounds";
         return;
     }
-    if (tighten_rounds(E, ne, nl, local, round_of, R1, 0x5EEDull ^ (uint64_t)(uint32_t)elems[0]))
-        R1 = (E + kRound - 1) / kRound;
+    // a round holds at most one element of each node, so a tile needs at
+    // least as many rounds as its busiest node has elements: the repair is
+    // tried only where the floor allows that
+    const int floor_rounds = (E + kRound - 1) / kRound;
+    const int max_valence = nl > 0 ? *std::max_element(valence.begin(), valence.end()) : 0;
+    if (max_valence <= floor_rounds &&
+        tighten_rounds(E, ne, nl, local, round_of, R1, 0x5EEDull ^ (uint64_t)(uint32_t)elems[0]))
+        R1 = floor_rounds;
     // P1 tiles are relabelled and arranged so that the warp-wide
     // shared-memory gathers are free of bank conflicts
     const bool arrange = in.arrange && in.elem_type != 2;
